@@ -1,0 +1,10 @@
+"""FP64 CPU oracle of the leaf-scattering FDTD hot path.
+
+TEST INFRASTRUCTURE. Only tests/, __graft_entry__.smoke() and bench.py's
+cpu_baseline / reference leg may import or run anything in this package. The
+CUDA library never routes through it, and it shares no code with the library.
+"""
+from .fdtd_tmz import (  # noqa: F401
+    C0, MU0, EPS0, ETA0, eps_sigma, lossy_coefficients, cpml_profile,
+    source_waveform, IncidentLine, TMzOracle, run_rt,
+)
