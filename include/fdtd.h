@@ -1,0 +1,192 @@
+/*
+ * libfdtd: 2D TMz FDTD of segmented leaf cross-sections on one GPU (sm_103a).
+ *
+ * Problem statement (arXiv 2512.17132, Sec. 2.1 and Sec. 2.6): given a 2D
+ * segmented cross-section (a label map), the grid step h and time step dt,
+ * the complex index n~ = n + i kappa of every tissue label at the run's
+ * wavelength and a normally incident plane wave, return the reflectance R
+ * and transmittance T at that wavelength.
+ *
+ * Discrete system (the same one the FP64 oracle implements):
+ *   - TMz Yee leapfrog of Sec. 2.3: Ez at cell centres (times n+1/2), Hx on
+ *     the top edge and Hy on the left edge of each cell (times n). Row j = 0
+ *     is the top row; rows grow along the incident wave (s = -y). Each step
+ *     updates Ez first, then Hx and Hy.
+ *   - Per-cell lossy coefficients (Sec. 2.2, Sec. 2.3): eps_r = n^2 - k^2,
+ *     sigma = 2 w0 eps0 n k, b = sigma dt/(2 eps0 eps_r),
+ *     Ez <- (1-b)/(1+b) Ez + dt/(eps0 eps_r (1+b)) curl H.
+ *   - Periodic columns (Sec. 2.4); a CFS-CPML of pml_cells rows at the top
+ *     and at the bottom (replacing the paper's split-field PML).
+ *   - TF/SF plane-wave source (Sec. 2.5): Ez rows >= tfsf_row and Hx rows
+ *     > tfsf_row hold the total field. The incident wave is the echo-free
+ *     1D air lattice driven by a hard source s(t) at its cell 0 and read at
+ *     its cell/edge 1.
+ *   - Running DFTs at w0 of Ez (rows r_row, t_row) and of the row-averaged
+ *     Hx (Sec. 2.6) give Poynting fluxes; R and T are normalised by the same
+ *     run on an empty (all-air) domain, which the library runs alongside.
+ *
+ * Storage on the device is FP32 with H kept as eta0*H; every field exchanged
+ * through this interface is in SI units (V/m and A/m), FP32, dense row-major
+ * (ny rows of nx values, x fastest), and may be host or device memory.
+ *
+ * All functions return FDTD_OK (0) or a negative FDTD_E* code; the message
+ * of the last failure on a handle is fdtd_last_error(handle), and failures
+ * of fdtd_create (no handle yet) are reported by fdtd_last_error(NULL) on
+ * the calling thread. Calls on one handle must not overlap (one host thread
+ * at a time); different handles are independent.
+ */
+#ifndef LIBFDTD_H
+#define LIBFDTD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FDTD_OK 0
+#define FDTD_EINVAL (-1)    /* invalid argument (message says which) */
+#define FDTD_ENOMEM (-2)    /* device or host allocation failed */
+#define FDTD_ECUDA (-3)     /* a CUDA call failed */
+#define FDTD_EUNSTABLE (-4) /* the watchdog saw a non-finite field */
+#define FDTD_ETIMEOUT (-5)  /* a bounded device-side wait gave up */
+#define FDTD_ESTATE (-6)    /* state buffer of the wrong size or layout */
+
+/* Grid and row layout. Rows: 0 <= pml_cells; pml_cells <= r_row < tfsf_row;
+ * tfsf_row < t_row; t_row + 1 < ny - pml_cells. The Courant number
+ * c0 dt / dx must not exceed 1/sqrt(2) (the 2D CFL limit of Sec. 2.3).
+ * CPML grading at depth d (cells, 0 at the interface, pml_cells at the outer
+ * wall): sigma = pml_sigma_max (d/L)^m, kappa = 1 + (pml_kappa_max-1)(d/L)^m,
+ * alpha = pml_alpha_max (1 - d/L), with m = pml_order. */
+typedef struct fdtd_grid {
+    int32_t nx, ny;          /* columns (periodic) and rows */
+    double dx, dt;           /* cell size [m] and time step [s] */
+    int32_t pml_cells;       /* CPML rows at the top and at the bottom */
+    int32_t tfsf_row;        /* first total-field Ez row */
+    int32_t r_row;           /* reflection monitor row (scattered field) */
+    int32_t t_row;           /* transmission monitor row (total field) */
+    double pml_order;        /* polynomial grading order m */
+    double pml_sigma_max;    /* [S/m] */
+    double pml_kappa_max;    /* >= 1 */
+    double pml_alpha_max;    /* [S/m] */
+} fdtd_grid;
+
+/* Complex refractive index n + i k of one label at the run's wavelength. */
+typedef struct fdtd_material {
+    double n, k;
+} fdtd_material;
+
+/* Incident waveform s(t) at the hard-source cell of the incident lattice:
+ * kind 0: exp(-(t-t0)^2/(2 tau^2)) sin(w0 (t-t0)) with amplitude-spectrum
+ *         FWHM = rel_bandwidth * f0, tau = 2 sqrt(2 ln 2)/(2 pi rel_bandwidth f0),
+ *         t0 = t0_over_tau * tau;
+ * kind 1: sin(w0 t) under a raised-cosine ramp over the first 10 periods;
+ * kind 2: no incident wave (fields come from fdtd_set_fields/load_state).
+ * w0 = 2 pi c0 / lambda0 is also the DFT frequency and the frequency at
+ * which sigma is evaluated. */
+typedef struct fdtd_source {
+    int32_t kind;
+    int32_t reserved;        /* must be 0 */
+    double lambda0;          /* [m] */
+    double rel_bandwidth;
+    double t0_over_tau;
+} fdtd_source;
+
+typedef struct fdtd_handle fdtd_handle;
+
+/* Per-handle counters. stencil_ms sums CUDA-event time over the stencil
+ * launches when FDTD_OPT_TIMING is on (0 otherwise); it is complete after
+ * fdtd_flux or fdtd_synchronize. */
+typedef struct fdtd_stats {
+    int64_t steps;            /* time steps taken */
+    int64_t stencil_launches; /* launches of the main field-update kernel */
+    int64_t total_launches;   /* all kernel launches of this handle */
+    double stencil_ms;        /* event-timed duration of those launches */
+    int32_t kernel;           /* stencil in use: 1 naive, 2 temporally blocked */
+    int32_t block_steps;      /* steps per blocked launch */
+    int32_t seg_rows;         /* rows per warp task of the blocked kernel */
+    int32_t reserved;
+} fdtd_stats;
+
+/* Options for fdtd_set_option. */
+#define FDTD_OPT_KERNEL 1      /* 0 auto, 1 per-half-step kernels, 2 temporally blocked */
+#define FDTD_OPT_BLOCK_STEPS 2 /* steps per blocked launch, 1..12 (default 8) */
+#define FDTD_OPT_SEG_ROWS 3    /* rows per warp task of the blocked kernel (0 = auto) */
+#define FDTD_OPT_TIMING 4      /* 1: time stencil launches with CUDA events */
+#define FDTD_OPT_WATCHDOG 5    /* check fields for non-finite values every N steps (0 off) */
+
+/* Create a simulation. grid, labels (ny*nx uint8, values < n_labels), table
+ * (n_labels entries, n > k >= 0) and source are copied; the caller keeps
+ * ownership of its buffers. labels may be host or device memory.
+ * cuda_stream: a cudaStream_t on the current device, or NULL for a stream
+ * owned by the handle. Device memory (about 2 x 12 bytes per cell plus the
+ * label map) is allocated here. The Ez rows tfsf_row-1 and tfsf_row must be
+ * air (n = 1, k = 0) so that the injected wave matches the air lattice.
+ * Errors: FDTD_EINVAL (layout, Courant number, labels, table), FDTD_ENOMEM,
+ * FDTD_ECUDA. On success *out is a new handle; on failure *out is NULL. */
+int fdtd_create(const fdtd_grid* grid, const uint8_t* labels,
+                const fdtd_material* table, int32_t n_labels,
+                const fdtd_source* source, void* cuda_stream,
+                fdtd_handle** out);
+
+/* Advance by `steps` (>= 0) leapfrog steps (Sec. 2.3), accumulating the
+ * monitor DFTs, and the empty-domain reference run by the same steps.
+ * Asynchronous on the handle's stream; host work (the incident-wave tables)
+ * overlaps the device work. */
+int fdtd_run(fdtd_handle* h, int64_t steps);
+
+/* Return to step 0: zero the fields, CPML auxiliaries, DFT accumulators and
+ * the empty-domain run; geometry, materials and tables are kept. Async. */
+int fdtd_reset(fdtd_handle* h);
+
+/* Wait for all work of the handle; reports watchdog and timeout flags. */
+int fdtd_synchronize(fdtd_handle* h);
+
+/* Reflectance and transmittance at lambda0 from the DFTs accumulated so far
+ * (Sec. 2.6, Poynting form): R = P_up(r_row)/P_inc, T = P_down(t_row)/P_inc,
+ * P_inc = nx * P_down(t_row) of the empty-domain run. Synchronises. */
+int fdtd_flux(fdtd_handle* h, double* R, double* T);
+
+/* The three fluxes behind R and T in W/m (per unit z length):
+ * out[0] = P_up at r_row, out[1] = P_down at t_row, out[2] = P_inc. */
+int fdtd_flux_raw(fdtd_handle* h, double out[3]);
+
+/* Running DFT accumulators (Sec. 2.6) in SI units: 4 rows of nx complex
+ * values, each stored as (re, im) doubles (8*nx doubles in total, host or
+ * device), in the order Ez(r_row), Hx(r_row), Ez(t_row), Hx(t_row); the Hx
+ * rows average the edges row and row+1. */
+int fdtd_get_dft(fdtd_handle* h, double* out);
+
+/* Read or overwrite the fields (SI, FP32, ny*nx each, host or device; a NULL
+ * pointer skips that field). Hx row 0 is the fixed top edge and reads 0;
+ * fdtd_set_fields forces it to 0. Synchronous. */
+int fdtd_get_fields(fdtd_handle* h, float* ez, float* hx, float* hy);
+int fdtd_set_fields(fdtd_handle* h, const float* ez, const float* hx,
+                    const float* hy);
+
+/* Complete simulation state (fields, CPML auxiliaries, DFT accumulators,
+ * empty-domain run, step count) for checkpoint / restart. The buffer (host
+ * or device) must hold fdtd_state_bytes(h) bytes; load requires a handle
+ * created with the same grid. */
+size_t fdtd_state_bytes(const fdtd_handle* h);
+int fdtd_save_state(fdtd_handle* h, void* buf, size_t bytes);
+int fdtd_load_state(fdtd_handle* h, const void* buf, size_t bytes);
+
+/* Tuning and instrumentation switches (FDTD_OPT_*). */
+int fdtd_set_option(fdtd_handle* h, int32_t option, int64_t value);
+int fdtd_get_stats(fdtd_handle* h, fdtd_stats* out);
+
+/* Message of the last failure on h (or of fdtd_create on this thread when h
+ * is NULL); "" if none. Valid until the next call on h. */
+const char* fdtd_last_error(const fdtd_handle* h);
+
+/* Release the handle and its device memory (waits for its work). NULL is a
+ * no-op. */
+void fdtd_destroy(fdtd_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIBFDTD_H */

@@ -1,0 +1,80 @@
+// Device-side update arithmetic shared by every field-update kernel of the
+// library, so that the per-half-step kernels, the temporally blocked kernel
+// and the empty-domain column kernel round identically (explicit _rn
+// intrinsics keep the compiler from contracting them differently).
+//
+// Units: Ez in V/m, H stored as eta0*H (V/m). With S = c0 dt/dx the TMz
+// updates of Sec. 2.3 become
+//   Ez <- ca Ez + cb [ (Hy[i+1]-Hy[i]) + (Hx[j+1]-Hx[j]) ]
+//   Hx <- Hx + S (Ez[j] - Ez[j-1]),   Hy <- Hy + S (Ez[i] - Ez[i-1])
+// with ca = (1-b)/(1+b), cb = S/(eps_r (1+b)), b = sigma dt/(2 eps0 eps_r).
+// In CPML rows the s-derivative d is replaced by d/kappa + psi with
+// psi <- b_pml psi + c_pml d (Roden-Gedney recursive convolution).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fdtd {
+
+__device__ __forceinline__ float ez_new(float ca, float cb, float e, float dhy, float dhx) {
+    return __fmaf_rn(cb, __fadd_rn(dhy, dhx), __fmul_rn(ca, e));
+}
+
+__device__ __forceinline__ float ez_new_pml(float ca, float cb, float e, float dhy,
+                                            float dhx, float ik, float psi) {
+    return __fmaf_rn(cb, __fadd_rn(dhy, __fmaf_rn(dhx, ik, psi)), __fmul_rn(ca, e));
+}
+
+__device__ __forceinline__ float psi_new(float b, float c, float psi, float d) {
+    return __fmaf_rn(b, psi, __fmul_rn(c, d));
+}
+
+__device__ __forceinline__ float h_new(float h, float S, float d) {
+    return __fmaf_rn(S, d, h);
+}
+
+__device__ __forceinline__ float h_new_pml(float h, float S, float d, float ik, float psi) {
+    return __fmaf_rn(S, __fmaf_rn(d, ik, psi), h);
+}
+
+// Row-averaged Hx at a monitor row: edges row and row+1.
+__device__ __forceinline__ float hx_avg(float a, float b) {
+    return __fmul_rn(0.5f, __fadd_rn(a, b));
+}
+
+__device__ __forceinline__ void dft_add(double2* acc, float v, double2 ph) {
+    double2 a = *acc;
+    a.x = fma((double)v, ph.x, a.x);
+    a.y = fma((double)v, ph.y, a.y);
+    *acc = a;
+}
+
+// Arguments common to the field-update kernels.
+struct StepArgs {
+    int nx, ny;
+    int pitch;            // floats per field row (multiple of 32)
+    int lpitch;           // bytes per label row (multiple of 16)
+    int P;                // CPML rows per side
+    int js, jr, jt;       // TF/SF row, monitor rows
+    int n_labels;
+    float S;              // Courant number c0 dt / dx
+    const uint8_t* labels;
+    const float2* coef;   // (ca, cb) per label
+    const float* pml_e;   // [3][2P]: b, c, 1/kappa for Ez rows (top 0..P-1, then bottom)
+    const float* pml_h;   // [3][2P]: same for Hx rows
+    const float* hinc;    // incident eta0*Hx at edge tfsf_row, per absolute step
+    const float* einc;    // incident Ez at cell tfsf_row, per absolute step
+    const double2* phE;   // e^{i w0 (n+1/2) dt}
+    const double2* phH;   // e^{i w0 (n+1) dt}
+    double2* dft;         // [4][nx]: Ez(jr), Hx(jr), Ez(jt), Hx(jt)
+};
+
+// Index of a CPML row within the [2P] tables and psi arrays, or -1.
+__device__ __forceinline__ int pml_e_index(int j, int ny, int P) {
+    return (j < P) ? j : ((j >= ny - P) ? (P + j - (ny - P)) : -1);
+}
+__device__ __forceinline__ int pml_h_index(int j, int ny, int P) {
+    return (j < P) ? j : ((j >= ny - P) ? (P + j - (ny - P)) : -1);
+}
+
+}  // namespace fdtd

@@ -1,0 +1,135 @@
+// Internal declarations of libfdtd: the handle, the incident-wave generator
+// and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/fdtd.h"
+#include "fdtd_device.cuh"
+
+namespace fdtd {
+
+// Echo-free incident lattice (Sec. 2.5), FP64 on the host, H kept as eta0*H.
+// Cell 0 is a hard source s(t); the TF/SF line reads Ez at cell 1 (time
+// n+1/2) and eta0*Hx at edge 1 (time n). A signal moves at most one cell per
+// step, so at step m only cells k <= m+2 can be non-zero, and only cells
+// k <= plan_end - m + 2 can still reach cell 1 before step plan_end; the
+// update is limited to both bounds, which leaves every recorded value
+// exactly as on an unbounded lattice.
+struct IncidentGen {
+    double S = 0, dt = 0, lambda0 = 0, bw = 0, t0_over_tau = 0;
+    int kind = 0;
+    int64_t plan_end = 0;  // values are exact for steps < plan_end
+    int64_t m = 0;         // next step to produce
+    std::vector<double> ez, hx;
+    void reset(int64_t plan);
+    double source(double t) const;
+    void step(float* hinc, float* einc);
+};
+
+// Segment plan of the temporally blocked kernel for one block depth.
+struct BlockPlan {
+    int K = 0;            // steps per launch
+    int halo = 0;         // halo columns per strip side
+    int w_int = 0;        // interior columns per strip
+    int n_strips = 0;
+    int n_segs = 0;
+    int seg_rows = 0;
+    int* d_seg_y0 = nullptr;  // n_segs + 1 row boundaries
+};
+
+struct BlockedArgs {
+    StepArgs s;
+    const float* ez_in; const float* hx_in; const float* hy_in;
+    float* ez_out; float* hx_out; float* hy_out;
+    const float* psiE_in; const float* psiH_in;
+    float* psiE_out; float* psiH_out;
+    float* slotE; float* slotH;   // per-strip CPML carries [n_strips][2][P][128]
+    const int* seg_y0;
+    int n_strips, n_tasks, w_int;
+};
+
+struct TwinArgs {
+    int ny, P, js, jr, jt;
+    float S, ca, cb;      // air coefficients
+    const float* pml_e; const float* pml_h;
+    const float* hinc; const float* einc;
+    const double2* phE; const double2* phH;
+    float* ez; float* hx; float* psiE; float* psiH;
+    double2* dft;         // [4]: Ez(jr), Hx(jr), Ez(jt), Hx(jt)
+};
+
+// launchers (kernels.cu, blocked.cu)
+void launch_naive_step(const StepArgs& a, float* ez, float* hx, float* hy,
+                       float* psiE, float* psiH, int64_t n, cudaStream_t st);
+void launch_twin(const TwinArgs& a, int64_t n0, int steps, cudaStream_t st);
+void launch_flux(const double2* dft, const double2* twin_dft, int nx, double* out,
+                 cudaStream_t st);
+void launch_pack(const float* src, int pitch, int nx, int ny, float scale, float* dst,
+                 cudaStream_t st);
+void launch_unpack(const float* src, int nx, int ny, float scale, float* dst, int pitch,
+                   cudaStream_t st);
+void launch_scale_double(double* p, int64_t n, double scale, cudaStream_t st);
+void launch_check_finite(const float* p, int pitch, int nx, int ny, int* flag,
+                         cudaStream_t st);
+bool launch_blocked(const BlockedArgs& a, int K, int64_t n0, cudaStream_t st);
+int blocked_max_K();
+
+}  // namespace fdtd
+
+struct fdtd_handle {
+    fdtd_grid g{};
+    fdtd_source src{};
+    int n_labels = 0;
+    double S = 0, omega = 0;
+    cudaStream_t stream = nullptr, twin_stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    int pitch = 0, lpitch = 0;
+    // device state
+    float* ez[2] = {nullptr, nullptr};
+    float* hx[2] = {nullptr, nullptr};
+    float* hy[2] = {nullptr, nullptr};
+    float* psiE[2] = {nullptr, nullptr};
+    float* psiH[2] = {nullptr, nullptr};
+    int cur = 0;
+    uint8_t* labels = nullptr;
+    float2* coef = nullptr;
+    float* pml_e = nullptr;
+    float* pml_h = nullptr;
+    double2* dft = nullptr;
+    float* tw_ez = nullptr; float* tw_hx = nullptr;
+    float* tw_psiE = nullptr; float* tw_psiH = nullptr;
+    double2* tw_dft = nullptr;
+    double* d_flux = nullptr;
+    double* h_flux = nullptr;  // pinned
+    int* d_flag = nullptr;
+    float* slotE = nullptr; float* slotH = nullptr;
+    size_t slot_floats = 0;
+    // incident-wave and phase tables (absolute step index)
+    fdtd::IncidentGen gen;
+    int64_t tab_cap = 0;
+    float* d_hinc = nullptr; float* d_einc = nullptr;
+    double2* d_phE = nullptr; double2* d_phH = nullptr;
+    float* h_hinc = nullptr; float* h_einc = nullptr;      // pinned
+    double2* h_phE = nullptr; double2* h_phH = nullptr;    // pinned
+    int64_t tab_uploaded = 0;   // table entries [0, tab_uploaded) are on the device
+    cudaEvent_t ev_tab = nullptr, ev_twin = nullptr;
+    // blocked-kernel plans per depth
+    std::vector<fdtd::BlockPlan> plans;
+    // options
+    int opt_kernel = 0, opt_block = 8, opt_seg = 0, opt_timing = 0;
+    int64_t opt_watchdog = 0;
+    // stats
+    int64_t n = 0;
+    int64_t stencil_launches = 0, total_launches = 0;
+    double stencil_ms = 0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> timing_events;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> event_pool;
+    int last_kernel = 0;
+    std::string err;
+};

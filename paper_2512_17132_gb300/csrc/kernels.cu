@@ -1,0 +1,221 @@
+// Per-half-step field kernels, the empty-domain column kernel, the flux
+// reduction and the field pack/unpack kernels.
+#include <cuda_runtime.h>
+
+#include "fdtd_internal.h"
+
+namespace fdtd {
+
+// Ez^{n-1/2} -> Ez^{n+1/2} on every cell (Sec. 2.3, TMz Ez update), with the
+// CPML recursion in the top/bottom rows and the TF/SF correction at js.
+__global__ void k_naive_e(StepArgs a, float* __restrict__ ez, const float* __restrict__ hx,
+                          const float* __restrict__ hy, float* __restrict__ psiE, int64_t n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= a.nx) return;
+    const size_t o = (size_t)j * a.pitch + i;
+    const int ir = (i + 1 == a.nx) ? 0 : i + 1;                       // periodic x
+    const float dhy = __fsub_rn(hy[(size_t)j * a.pitch + ir], hy[o]);
+    const float hxb = (j + 1 < a.ny) ? hx[o + a.pitch] : 0.0f;         // Hx[ny] = 0
+    float dhx = __fsub_rn(hxb, hx[o]);
+    if (j == a.js) dhx = __fsub_rn(dhx, a.hinc[n]);                    // TF cell sees total Hx
+    const float2 c = a.coef[a.labels[(size_t)j * a.lpitch + i]];
+    const float e = ez[o];
+    const int pj = pml_e_index(j, a.ny, a.P);
+    if (pj >= 0) {
+        const float b = a.pml_e[pj], cc = a.pml_e[2 * a.P + pj], ik = a.pml_e[4 * a.P + pj];
+        float* pp = psiE + (size_t)pj * a.pitch + i;
+        const float p = psi_new(b, cc, *pp, dhx);
+        *pp = p;
+        ez[o] = ez_new_pml(c.x, c.y, e, dhy, dhx, ik, p);
+    } else {
+        ez[o] = ez_new(c.x, c.y, e, dhy, dhx);
+    }
+}
+
+// H^n -> H^{n+1} (Sec. 2.3, TMz Hx and Hy updates). Hx row 0 stays 0.
+__global__ void k_naive_h(StepArgs a, const float* __restrict__ ez, float* __restrict__ hx,
+                          float* __restrict__ hy, float* __restrict__ psiH, int64_t n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= a.nx) return;
+    const size_t o = (size_t)j * a.pitch + i;
+    const int il = (i == 0) ? a.nx - 1 : i - 1;                        // periodic x
+    const float e = ez[o];
+    hy[o] = h_new(hy[o], a.S, __fsub_rn(e, ez[(size_t)j * a.pitch + il]));
+    if (j > 0) {
+        float d = __fsub_rn(e, ez[o - a.pitch]);
+        if (j == a.js) d = __fsub_rn(d, a.einc[n]);                    // SF edge sees scattered Ez
+        const int pj = pml_h_index(j, a.ny, a.P);
+        if (pj >= 0) {
+            const float b = a.pml_h[pj], cc = a.pml_h[2 * a.P + pj], ik = a.pml_h[4 * a.P + pj];
+            float* pp = psiH + (size_t)pj * a.pitch + i;
+            const float p = psi_new(b, cc, *pp, d);
+            *pp = p;
+            hx[o] = h_new_pml(hx[o], a.S, d, ik, p);
+        } else {
+            hx[o] = h_new(hx[o], a.S, d);
+        }
+    }
+}
+
+// Running DFT of the monitor rows after step n (Sec. 2.6).
+__global__ void k_naive_dft(StepArgs a, const float* __restrict__ ez,
+                            const float* __restrict__ hx, int64_t n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.nx) return;
+    const int w = blockIdx.y;
+    const int row = w ? a.jt : a.jr;
+    const size_t o = (size_t)row * a.pitch + i;
+    dft_add(&a.dft[(size_t)(2 * w) * a.nx + i], ez[o], a.phE[n]);
+    dft_add(&a.dft[(size_t)(2 * w + 1) * a.nx + i], hx_avg(hx[o], hx[o + a.pitch]), a.phH[n]);
+}
+
+void launch_naive_step(const StepArgs& a, float* ez, float* hx, float* hy, float* psiE,
+                       float* psiH, int64_t n, cudaStream_t st) {
+    dim3 blk(256);
+    dim3 grd((a.nx + 255) / 256, a.ny);
+    k_naive_e<<<grd, blk, 0, st>>>(a, ez, hx, hy, psiE, n);
+    k_naive_h<<<grd, blk, 0, st>>>(a, ez, hx, hy, psiH, n);
+    k_naive_dft<<<dim3((a.nx + 255) / 256, 2), blk, 0, st>>>(a, ez, hx, n);
+}
+
+// Empty-domain reference run: one column of air (an x-uniform field has
+// Hy = 0 and needs a single column), same rows, CPML, source and monitors.
+// One block advances `steps` steps; the column lives in global memory.
+__global__ void __launch_bounds__(1024) k_twin(TwinArgs a, int64_t n0, int steps) {
+    const int ny = a.ny;
+    for (int s = 0; s < steps; ++s) {
+        const int64_t n = n0 + s;
+        const float hinc = a.hinc[n], einc = a.einc[n];
+        for (int j = threadIdx.x; j < ny; j += blockDim.x) {
+            const float hxb = (j + 1 < ny) ? a.hx[j + 1] : 0.0f;
+            float dhx = __fsub_rn(hxb, a.hx[j]);
+            if (j == a.js) dhx = __fsub_rn(dhx, hinc);
+            const float e = a.ez[j];
+            const int pj = pml_e_index(j, ny, a.P);
+            if (pj >= 0) {
+                const float p = psi_new(a.pml_e[pj], a.pml_e[2 * a.P + pj], a.psiE[pj], dhx);
+                a.psiE[pj] = p;
+                a.ez[j] = ez_new_pml(a.ca, a.cb, e, 0.0f, dhx, a.pml_e[4 * a.P + pj], p);
+            } else {
+                a.ez[j] = ez_new(a.ca, a.cb, e, 0.0f, dhx);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            dft_add(&a.dft[0], a.ez[a.jr], a.phE[n]);
+            dft_add(&a.dft[2], a.ez[a.jt], a.phE[n]);
+        }
+        for (int j = threadIdx.x + 1; j < ny; j += blockDim.x) {
+            float d = __fsub_rn(a.ez[j], a.ez[j - 1]);
+            if (j == a.js) d = __fsub_rn(d, einc);
+            const int pj = pml_h_index(j, ny, a.P);
+            if (pj >= 0) {
+                const float p = psi_new(a.pml_h[pj], a.pml_h[2 * a.P + pj], a.psiH[pj], d);
+                a.psiH[pj] = p;
+                a.hx[j] = h_new_pml(a.hx[j], a.S, d, a.pml_h[4 * a.P + pj], p);
+            } else {
+                a.hx[j] = h_new(a.hx[j], a.S, d);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            dft_add(&a.dft[1], hx_avg(a.hx[a.jr], a.hx[a.jr + 1]), a.phH[n]);
+            dft_add(&a.dft[3], hx_avg(a.hx[a.jt], a.hx[a.jt + 1]), a.phH[n]);
+        }
+    }
+}
+
+void launch_twin(const TwinArgs& a, int64_t n0, int steps, cudaStream_t st) {
+    k_twin<<<1, 1024, 0, st>>>(a, n0, steps);
+}
+
+// Flux sums (Sec. 2.6, Poynting form): out[0] = sum_i Re(E_r conj(H_r)),
+// out[1] = sum_i Re(E_t conj(H_t)), out[2] = Re(E_t conj(H_t)) of the empty
+// column. Warp-shuffle then shared-memory reduction in a fixed order.
+__global__ void __launch_bounds__(1024) k_flux(const double2* __restrict__ dft,
+                                               const double2* __restrict__ tw, int nx,
+                                               double* out) {
+    __shared__ double sh[2][32];
+    double ar = 0.0, at = 0.0;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        const double2 er = dft[i], hr = dft[nx + i], et = dft[2 * nx + i], ht = dft[3 * nx + i];
+        ar += er.x * hr.x + er.y * hr.y;
+        at += et.x * ht.x + et.y * ht.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ar += __shfl_down_sync(0xffffffffu, ar, o);
+        at += __shfl_down_sync(0xffffffffu, at, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { sh[0][w] = ar; sh[1][w] = at; }
+    __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        ar = (l < nw) ? sh[0][l] : 0.0;
+        at = (l < nw) ? sh[1][l] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            ar += __shfl_down_sync(0xffffffffu, ar, o);
+            at += __shfl_down_sync(0xffffffffu, at, o);
+        }
+        if (l == 0) {
+            out[0] = ar;
+            out[1] = at;
+            out[2] = tw[2].x * tw[3].x + tw[2].y * tw[3].y;
+        }
+    }
+}
+
+void launch_flux(const double2* dft, const double2* twin_dft, int nx, double* out,
+                 cudaStream_t st) {
+    k_flux<<<1, 1024, 0, st>>>(dft, twin_dft, nx, out);
+}
+
+__global__ void k_pack(const float* __restrict__ src, int pitch, int nx, int ny, float scale,
+                       float* __restrict__ dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i < nx) dst[(size_t)j * nx + i] = src[(size_t)j * pitch + i] * scale;
+}
+
+__global__ void k_unpack(const float* __restrict__ src, int nx, int ny, float scale,
+                         float* __restrict__ dst, int pitch) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i < nx) dst[(size_t)j * pitch + i] = src[(size_t)j * nx + i] * scale;
+}
+
+void launch_pack(const float* src, int pitch, int nx, int ny, float scale, float* dst,
+                 cudaStream_t st) {
+    k_pack<<<dim3((nx + 255) / 256, ny), 256, 0, st>>>(src, pitch, nx, ny, scale, dst);
+}
+
+void launch_unpack(const float* src, int nx, int ny, float scale, float* dst, int pitch,
+                   cudaStream_t st) {
+    k_unpack<<<dim3((nx + 255) / 256, ny), 256, 0, st>>>(src, nx, ny, scale, dst, pitch);
+}
+
+__global__ void k_scale_double(double* p, int64_t n, double s) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] *= s;
+}
+
+void launch_scale_double(double* p, int64_t n, double scale, cudaStream_t st) {
+    if (n > 0) k_scale_double<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, n, scale);
+}
+
+// Watchdog: sets *flag when any Ez value is not finite.
+__global__ void k_check_finite(const float* __restrict__ p, int pitch, int nx, int ny,
+                               int* flag) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i < nx && !isfinite(p[(size_t)j * pitch + i])) atomicOr(flag, 1);
+}
+
+void launch_check_finite(const float* p, int pitch, int nx, int ny, int* flag,
+                         cudaStream_t st) {
+    k_check_finite<<<dim3((nx + 255) / 256, ny), 256, 0, st>>>(p, pitch, nx, ny, flag);
+}
+
+}  // namespace fdtd

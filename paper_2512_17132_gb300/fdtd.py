@@ -1,0 +1,283 @@
+"""ctypes binding of libfdtd (include/fdtd.h): same names, argument
+marshalling only. Every step of the FDTD path runs in the CUDA library; if
+the library is missing this module raises instead of falling back.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfdtd.so")
+
+FDTD_OK, FDTD_EINVAL, FDTD_ENOMEM, FDTD_ECUDA = 0, -1, -2, -3
+FDTD_EUNSTABLE, FDTD_ETIMEOUT, FDTD_ESTATE = -4, -5, -6
+FDTD_OPT_KERNEL, FDTD_OPT_BLOCK_STEPS, FDTD_OPT_SEG_ROWS = 1, 2, 3
+FDTD_OPT_TIMING, FDTD_OPT_WATCHDOG = 4, 5
+KERNEL_AUTO, KERNEL_NAIVE, KERNEL_BLOCKED = 0, 1, 2
+
+
+class fdtd_grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("dx", C.c_double), ("dt", C.c_double),
+                ("pml_cells", C.c_int32), ("tfsf_row", C.c_int32), ("r_row", C.c_int32),
+                ("t_row", C.c_int32), ("pml_order", C.c_double), ("pml_sigma_max", C.c_double),
+                ("pml_kappa_max", C.c_double), ("pml_alpha_max", C.c_double)]
+
+
+class fdtd_material(C.Structure):
+    _fields_ = [("n", C.c_double), ("k", C.c_double)]
+
+
+class fdtd_source(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("lambda0", C.c_double),
+                ("rel_bandwidth", C.c_double), ("t0_over_tau", C.c_double)]
+
+
+class fdtd_stats(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("stencil_launches", C.c_int64),
+                ("total_launches", C.c_int64), ("stencil_ms", C.c_double),
+                ("kernel", C.c_int32), ("block_steps", C.c_int32), ("seg_rows", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class FDTDError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libfdtd error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libfdtd.so (built by paper_2512_17132_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FileNotFoundError(
+            f"{path} is missing: build it with paper_2512_17132_gb300.build.build()")
+    lib = C.CDLL(path)
+    vp, i32, i64, dp = C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_double)
+    sig = {
+        "fdtd_create": (C.c_int, [C.POINTER(fdtd_grid), vp, C.POINTER(fdtd_material), i32,
+                                  C.POINTER(fdtd_source), vp, C.POINTER(vp)]),
+        "fdtd_run": (C.c_int, [vp, i64]),
+        "fdtd_synchronize": (C.c_int, [vp]),
+        "fdtd_reset": (C.c_int, [vp]),
+        "fdtd_flux": (C.c_int, [vp, dp, dp]),
+        "fdtd_flux_raw": (C.c_int, [vp, dp]),
+        "fdtd_get_dft": (C.c_int, [vp, vp]),
+        "fdtd_get_fields": (C.c_int, [vp, vp, vp, vp]),
+        "fdtd_set_fields": (C.c_int, [vp, vp, vp, vp]),
+        "fdtd_state_bytes": (C.c_size_t, [vp]),
+        "fdtd_save_state": (C.c_int, [vp, vp, C.c_size_t]),
+        "fdtd_load_state": (C.c_int, [vp, vp, C.c_size_t]),
+        "fdtd_set_option": (C.c_int, [vp, i32, i64]),
+        "fdtd_get_stats": (C.c_int, [vp, C.POINTER(fdtd_stats)]),
+        "fdtd_last_error": (C.c_char_p, [vp]),
+        "fdtd_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(code, h):
+    if code != FDTD_OK:
+        msg = load_library().fdtd_last_error(h)
+        raise FDTDError(code, msg.decode() if msg else "")
+
+
+def _ptr(x):
+    """Device or host pointer of a numpy array or a torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return C.c_void_p(x.data_ptr())
+    return C.c_void_p(x.ctypes.data)
+
+
+def make_grid(spec) -> fdtd_grid:
+    return fdtd_grid(int(spec.nx), int(spec.ny), float(spec.dx), float(spec.dt),
+                     int(spec.pml_cells), int(spec.tfsf_row), int(spec.r_row), int(spec.t_row),
+                     float(spec.pml_order), float(spec.pml_sigma_max),
+                     float(spec.pml_kappa_max), float(spec.pml_alpha_max))
+
+
+def make_source(spec) -> fdtd_source:
+    return fdtd_source(int(spec.source_kind), 0, float(spec.lambda0),
+                       float(spec.rel_bandwidth), float(spec.t0_over_tau))
+
+
+def fdtd_create(grid: fdtd_grid, labels, materials, source: fdtd_source, stream=None):
+    """labels: (ny, nx) uint8 numpy array (host) or torch uint8 tensor (device);
+    materials: (n_labels, 2) array of (n, k). Returns an opaque handle."""
+    lib = load_library()
+    if not hasattr(labels, "data_ptr"):
+        labels = np.ascontiguousarray(labels, dtype=np.uint8)
+    mats = np.ascontiguousarray(materials, dtype=np.float64).reshape(-1, 2)
+    table = (fdtd_material * len(mats))(*[fdtd_material(float(n), float(k)) for n, k in mats])
+    out = C.c_void_p()
+    st = C.c_void_p(stream) if isinstance(stream, int) else (
+        C.c_void_p(stream.cuda_stream) if stream is not None else None)
+    code = lib.fdtd_create(C.byref(grid), _ptr(labels), table, len(mats), C.byref(source), st,
+                           C.byref(out))
+    _check(code, None)
+    return out
+
+
+def fdtd_run(h, steps: int):
+    _check(load_library().fdtd_run(h, int(steps)), h)
+
+
+def fdtd_reset(h):
+    _check(load_library().fdtd_reset(h), h)
+
+
+def fdtd_synchronize(h):
+    _check(load_library().fdtd_synchronize(h), h)
+
+
+def fdtd_flux(h):
+    R, T = C.c_double(), C.c_double()
+    _check(load_library().fdtd_flux(h, C.byref(R), C.byref(T)), h)
+    return R.value, T.value
+
+
+def fdtd_flux_raw(h):
+    out = (C.c_double * 3)()
+    _check(load_library().fdtd_flux_raw(h, out), h)
+    return tuple(out)
+
+
+def fdtd_get_dft(h, nx: int):
+    out = np.empty(8 * nx, dtype=np.float64)
+    _check(load_library().fdtd_get_dft(h, _ptr(out)), h)
+    z = out.reshape(4, nx, 2)
+    return z[..., 0] + 1j * z[..., 1]
+
+
+def fdtd_get_fields(h, ny: int, nx: int, out=None):
+    """Returns (ez, hx, hy) float32 SI arrays (host), or fills `out` tensors."""
+    if out is None:
+        out = tuple(np.empty((ny, nx), dtype=np.float32) for _ in range(3))
+    _check(load_library().fdtd_get_fields(h, *[_ptr(x) for x in out]), h)
+    return out
+
+
+def fdtd_set_fields(h, ez=None, hx=None, hy=None):
+    args = []
+    for x in (ez, hx, hy):
+        if x is not None and not hasattr(x, "data_ptr"):
+            x = np.ascontiguousarray(x, dtype=np.float32)
+        args.append(x)
+    _check(load_library().fdtd_set_fields(h, *[_ptr(x) for x in args]), h)
+
+
+def fdtd_state_bytes(h) -> int:
+    return int(load_library().fdtd_state_bytes(h))
+
+
+def fdtd_save_state(h, buf=None):
+    n = fdtd_state_bytes(h)
+    if buf is None:
+        buf = np.empty(n, dtype=np.uint8)
+    _check(load_library().fdtd_save_state(h, _ptr(buf), n), h)
+    return buf
+
+
+def fdtd_load_state(h, buf):
+    n = buf.numel() if hasattr(buf, "numel") else buf.nbytes
+    _check(load_library().fdtd_load_state(h, _ptr(buf), n), h)
+
+
+def fdtd_set_option(h, option: int, value: int):
+    _check(load_library().fdtd_set_option(h, int(option), int(value)), h)
+
+
+def fdtd_get_stats(h) -> dict:
+    st = fdtd_stats()
+    _check(load_library().fdtd_get_stats(h, C.byref(st)), h)
+    return {k: getattr(st, k) for k, _ in fdtd_stats._fields_ if k != "reserved"}
+
+
+def fdtd_last_error(h=None) -> str:
+    m = load_library().fdtd_last_error(h)
+    return m.decode() if m else ""
+
+
+def fdtd_destroy(h):
+    if h:
+        load_library().fdtd_destroy(h)
+
+
+class Simulation:
+    """Convenience owner of one handle, built from a run spec (an object with
+    the fields of fdtd_inputs.RunSpec)."""
+
+    def __init__(self, spec, stream=None, kernel: int = KERNEL_AUTO, block_steps=None,
+                 seg_rows=None, timing=False, labels=None):
+        self.spec = spec
+        lab = spec.labels if labels is None else labels
+        self.h = fdtd_create(make_grid(spec), lab, spec.materials, make_source(spec), stream)
+        try:
+            if kernel:
+                fdtd_set_option(self.h, FDTD_OPT_KERNEL, kernel)
+            if block_steps:
+                fdtd_set_option(self.h, FDTD_OPT_BLOCK_STEPS, block_steps)
+            if seg_rows:
+                fdtd_set_option(self.h, FDTD_OPT_SEG_ROWS, seg_rows)
+            if timing:
+                fdtd_set_option(self.h, FDTD_OPT_TIMING, 1)
+        except Exception:
+            self.close()
+            raise
+
+    def run(self, steps):
+        fdtd_run(self.h, steps)
+        return self
+
+    def reset(self):
+        fdtd_reset(self.h)
+        return self
+
+    def flux(self):
+        return fdtd_flux(self.h)
+
+    def flux_raw(self):
+        return fdtd_flux_raw(self.h)
+
+    def dft(self):
+        return fdtd_get_dft(self.h, self.spec.nx)
+
+    def fields(self):
+        return fdtd_get_fields(self.h, self.spec.ny, self.spec.nx)
+
+    def set_fields(self, ez=None, hx=None, hy=None):
+        fdtd_set_fields(self.h, ez, hx, hy)
+
+    def stats(self):
+        return fdtd_get_stats(self.h)
+
+    def close(self):
+        if self.h:
+            fdtd_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
