@@ -152,30 +152,52 @@ int sm_count(fdtd_handle* h) {
     return v;
 }
 
-// Segment plan of the blocked kernel for depth K (see blocked.cu).
+// Segment plan of the blocked kernel for depth K (see blocked.cu). One warp
+// task per (strip, segment); with W warps resident on the whole GPU, the
+// segment count is chosen to minimise waves x (rows per segment + 2K), the
+// cost model of a wave of equal tasks that each stream their rows plus
+// the K-row halos above and below.
 BlockPlan& get_plan(fdtd_handle* h, int K) {
     if ((int)h->plans.size() <= K) h->plans.resize(K + 1);
     BlockPlan& p = h->plans[K];
     const int want_seg = h->opt_seg;
-    if (p.K == K && p.d_seg_y0 && (want_seg == 0 || want_seg == p.seg_rows)) return p;
+    if (p.K == K && p.d_seg_y0 && p.variant == h->opt_variant &&
+        (want_seg == 0 || want_seg == p.seg_rows))
+        return p;
     dfree(p.d_seg_y0);
     const fdtd_grid& g = h->g;
     p.K = K;
+    p.variant = h->opt_variant;
     p.halo = (K + 3) / 4 * 4;
     p.w_int = 128 - 2 * p.halo;
     p.n_strips = (g.nx + p.w_int - 1) / p.w_int;
     const int P = g.pml_cells;
+    const int min_seg = P + K + 1;
     int seg = want_seg;
     if (seg <= 0) {
-        const int64_t target = (int64_t)sm_count(h) * 16;   // warps in flight
-        seg = (int)std::max<int64_t>(16, ((int64_t)g.ny * p.n_strips + target - 1) / target);
+        int per_sm = blocked_warps_per_sm(K, h->opt_variant);
+        if (per_sm <= 0) per_sm = 8;
+        const int64_t W = (int64_t)sm_count(h) * per_sm;
+        double best = 1e300;
+        seg = g.ny;
+        const int max_n = std::max(1, g.ny / min_seg);
+        for (int n = 1; n <= max_n; ++n) {
+            const int64_t tasks = (int64_t)n * p.n_strips;
+            const int64_t waves = (tasks + W - 1) / W;
+            const double rows = std::ceil((double)g.ny / n);
+            const double cost = (double)waves * (rows + 2.0 * K);
+            if (cost < best - 1e-9) {
+                best = cost;
+                seg = (int)rows;
+            }
+        }
     }
-    seg = std::max(seg, P + K + 1);
+    seg = std::max(seg, min_seg);
     std::vector<int> b{0};
     int pos = seg;
     while (pos < g.ny) {
         if (pos == g.r_row + 1 || pos == g.t_row + 1) ++pos;
-        if (g.ny - pos < P + K + 1) break;
+        if (g.ny - pos < min_seg) break;
         b.push_back(pos);
         pos += seg;
     }
@@ -234,7 +256,7 @@ void run_stencil(fdtd_handle* h, int64_t s, int64_t e, int kern) {
         b.n_strips = p.n_strips;
         b.n_tasks = p.n_strips * p.n_segs;
         b.w_int = p.w_int;
-        if (!launch_blocked(b, K, n, h->stream)) {
+        if (!launch_blocked(b, K, h->opt_variant, n, h->stream)) {
             h->err = "no blocked kernel instance for this depth";
             throw Fail{FDTD_EINVAL};
         }
@@ -823,6 +845,10 @@ int fdtd_set_option(fdtd_handle* h, int32_t option, int64_t value) {
         case FDTD_OPT_WATCHDOG:
             if (value < 0) break;
             h->opt_watchdog = value;
+            return FDTD_OK;
+        case FDTD_OPT_VARIANT:
+            if (value < 0 || value > 1) break;
+            h->opt_variant = (int)value;
             return FDTD_OK;
         default:
             break;

@@ -46,207 +46,293 @@ __device__ __forceinline__ void st4(float* p, const float (&v)[4]) {
 
 }  // namespace
 
+// Register state of one warp's pipeline: per level k the pending row
+// (Ez, Hx, Hy, 4 packed labels); level K keeps Ez and Hx of its last row.
 template <int K>
-__global__ void __launch_bounds__(128) k_blocked(const BlockedArgs a, const int64_t n0) {
-    constexpr int H = ((K + 3) / 4) * 4;
-    __shared__ float2 s_coef[256];
-    for (int t = threadIdx.x; t < a.s.n_labels; t += blockDim.x) s_coef[t] = a.s.coef[t];
-    __syncthreads();
+struct Pipe {
+    float E[K + 1][4], X[K + 1][4], Y[K][4];
+    uint32_t L[K];
+};
 
-    const int lane = threadIdx.x & 31;
-    const int task = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (task >= a.n_tasks) return;                 // whole warps leave together
-    const int strip = task % a.n_strips;
-    const int seg = task / a.n_strips;
-    const int y0 = a.seg_y0[seg], y1 = a.seg_y0[seg + 1];
-    const int nx = a.s.nx, ny = a.s.ny, P = a.s.P;
-    const size_t pitch = (size_t)a.s.pitch;
-    const size_t lpitch = (size_t)a.s.lpitch;
-    const float S = a.s.S;
-    const int xl = 4 * lane;                        // local column of the lane
-    const int xg_pre = strip * a.w_int - H + xl;    // global column before wrapping
-    const int gx = ((xg_pre % nx) + nx) % nx;       // nx % 4 == 0: 4 columns stay contiguous
-    const bool own = (xl >= H) && (xl < H + a.w_int) && (xg_pre < nx);
-    const bool own_r = (a.s.jr >= y0) && (a.s.jr < y1);
-    const bool own_t = (a.s.jt >= y0) && (a.s.jt < y1);
-    float* slotE = a.slotE + (size_t)strip * 2 * P * 128 + xl;
-    float* slotH = a.slotH + (size_t)strip * 2 * P * 128 + xl;
+struct Lane {
+    const float2* coef;
+    int gx, y0, y1, ny, P, nx;
+    bool own, own_r, own_t;
+    float S;
+};
 
-    float pE[K + 1][4], pX[K + 1][4], pY[K][4];
-    uint32_t pL[K];
+// One iteration of the pipeline: level k advances at row t-k-1, k = 0..K-1.
+// GENERAL = false is the lean path for iterations whose K rows hold no
+// CPML, source, monitor or boundary row and lie inside the valid range;
+// both paths round identically.
+template <int K, bool GENERAL>
+__device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[4],
+                                        float (&fY)[4], uint32_t& fL, const int t,
+                                        const BlockedArgs& a, const Lane& ln, float* slotE,
+                                        float* slotH, const int64_t n0) {
+    const float S = ln.S;
 #pragma unroll
-    for (int k = 0; k <= K; ++k) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            pE[k][q] = 0.f; pX[k][q] = 0.f;
-            if (k < K) pY[k][q] = 0.f;
+    for (int k = 0; k < K; ++k) {
+        const int r = t - k - 1;
+        float oE[4], oX[4], oY[4];
+        const uint32_t cL = p.L[k];
+        bool active = true;
+        if (GENERAL) {
+            const int lo = (ln.y0 == 0) ? 0 : (ln.y0 - K + k);
+            const int hi = min(ln.ny, ln.y1 + K - k - 1);
+            active = (r >= lo && r < hi);
         }
-        if (k < K) pL[k] = 0u;
-    }
-
-    const int t_begin = (y0 == 0) ? 0 : (y0 - K);
-    const int t_end = y1 + K;
-    for (int t = t_begin; t < t_end; ++t) {
-        float fE[4], fX[4], fY[4];
-        uint32_t fL;
-        if (t < ny) {
-            const size_t o = (size_t)t * pitch + gx;
-            ld4(a.ez_in + o, fE);
-            ld4(a.hx_in + o, fX);
-            ld4(a.hy_in + o, fY);
-            fL = __ldg(reinterpret_cast<const uint32_t*>(a.s.labels + (size_t)t * lpitch + gx));
-        } else {
+        if (active) {
+            const int64_t n = n0 + k;
+            const float yR = __shfl_down_sync(FULL, p.Y[k][0], 1);
+            const bool tf = GENERAL && (r == a.s.js);
+            const float hinc = tf ? a.s.hinc[n] : 0.f;
+            const int pe = GENERAL ? pml_e_index(r, ln.ny, ln.P) : -1;
+            if (GENERAL && pe >= 0) {
+                const float b = a.s.pml_e[pe], c = a.s.pml_e[2 * ln.P + pe];
+                const float ik = a.s.pml_e[4 * ln.P + pe];
+                float psi[4];
+                if (k == 0) ld4(a.psiE_in + (size_t)pe * a.s.pitch + ln.gx, psi);
+                else ld4_rw(slotE + (size_t)pe * 128, psi);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) { fE[q] = 0.f; fX[q] = 0.f; fY[q] = 0.f; }
-            fL = 0u;
-        }
+                for (int q = 0; q < 4; ++q) {
+                    const float2 cc = ln.coef[(cL >> (8 * q)) & 0xffu];
+                    const float dhy = __fsub_rn(q < 3 ? p.Y[k][q + 1] : yR, p.Y[k][q]);
+                    float dhx = __fsub_rn(fX[q], p.X[k][q]);
+                    if (tf) dhx = __fsub_rn(dhx, hinc);
+                    psi[q] = psi_new(b, c, psi[q], dhx);
+                    oE[q] = ez_new_pml(cc.x, cc.y, p.E[k][q], dhy, dhx, ik, psi[q]);
+                }
+                if (k == K - 1) {
+                    if (ln.own) st4(a.psiE_out + (size_t)pe * a.s.pitch + ln.gx, psi);
+                } else {
+                    st4(slotE + (size_t)pe * 128, psi);
+                }
+            } else {
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            const int r = t - k - 1;                 // row of level k+1 made here
-            const int lo = (y0 == 0) ? 0 : (y0 - K + k);
-            const int hi = min(ny, y1 + K - k - 1);
-            const int64_t n = n0 + k;                // absolute step of this level
-            float oE[4], oX[4], oY[4];
-            const uint32_t cL = pL[k];
-            if (r >= lo && r < hi) {
-                // ---- Ez^{n+1/2} at row r
-                const float yR = __shfl_down_sync(FULL, pY[k][0], 1);
-                const bool tf = (r == a.s.js);
-                const float hinc = tf ? a.s.hinc[n] : 0.f;
-                const int pe = pml_e_index(r, ny, P);
-                if (pe >= 0) {
-                    const float b = a.s.pml_e[pe], c = a.s.pml_e[2 * P + pe];
-                    const float ik = a.s.pml_e[4 * P + pe];
+                for (int q = 0; q < 4; ++q) {
+                    const float2 cc = ln.coef[(cL >> (8 * q)) & 0xffu];
+                    const float dhy = __fsub_rn(q < 3 ? p.Y[k][q + 1] : yR, p.Y[k][q]);
+                    float dhx = __fsub_rn(fX[q], p.X[k][q]);
+                    if (tf) dhx = __fsub_rn(dhx, hinc);
+                    oE[q] = ez_new(cc.x, cc.y, p.E[k][q], dhy, dhx);
+                }
+            }
+            if (!GENERAL || r > 0) {
+                const float einc = tf ? a.s.einc[n] : 0.f;
+                const int ph = GENERAL ? pml_h_index(r, ln.ny, ln.P) : -1;
+                if (GENERAL && ph >= 0) {
+                    const float b = a.s.pml_h[ph], c = a.s.pml_h[2 * ln.P + ph];
+                    const float ik = a.s.pml_h[4 * ln.P + ph];
                     float psi[4];
-                    if (k == 0) ld4(a.psiE_in + (size_t)pe * pitch + gx, psi);
-                    else ld4_rw(slotE + (size_t)pe * 128, psi);
+                    if (k == 0) ld4(a.psiH_in + (size_t)ph * a.s.pitch + ln.gx, psi);
+                    else ld4_rw(slotH + (size_t)ph * 128, psi);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const float2 cc = s_coef[(cL >> (8 * q)) & 0xffu];
-                        const float dhy = __fsub_rn(q < 3 ? pY[k][q + 1] : yR, pY[k][q]);
-                        float dhx = __fsub_rn(fX[q], pX[k][q]);
-                        if (tf) dhx = __fsub_rn(dhx, hinc);
-                        psi[q] = psi_new(b, c, psi[q], dhx);
-                        oE[q] = ez_new_pml(cc.x, cc.y, pE[k][q], dhy, dhx, ik, psi[q]);
+                        float d = __fsub_rn(oE[q], p.E[k + 1][q]);
+                        if (tf) d = __fsub_rn(d, einc);
+                        psi[q] = psi_new(b, c, psi[q], d);
+                        oX[q] = h_new_pml(p.X[k][q], S, d, ik, psi[q]);
                     }
                     if (k == K - 1) {
-                        if (own) st4(a.psiE_out + (size_t)pe * pitch + gx, psi);
+                        if (ln.own) st4(a.psiH_out + (size_t)ph * a.s.pitch + ln.gx, psi);
                     } else {
-                        st4(slotE + (size_t)pe * 128, psi);
+                        st4(slotH + (size_t)ph * 128, psi);
                     }
                 } else {
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const float2 cc = s_coef[(cL >> (8 * q)) & 0xffu];
-                        const float dhy = __fsub_rn(q < 3 ? pY[k][q + 1] : yR, pY[k][q]);
-                        float dhx = __fsub_rn(fX[q], pX[k][q]);
-                        if (tf) dhx = __fsub_rn(dhx, hinc);
-                        oE[q] = ez_new(cc.x, cc.y, pE[k][q], dhy, dhx);
-                    }
-                }
-                // ---- Hx^{n+1} at edge r (edge 0 is fixed)
-                if (r > 0) {
-                    const float einc = tf ? a.s.einc[n] : 0.f;
-                    const int ph = pml_h_index(r, ny, P);
-                    if (ph >= 0) {
-                        const float b = a.s.pml_h[ph], c = a.s.pml_h[2 * P + ph];
-                        const float ik = a.s.pml_h[4 * P + ph];
-                        float psi[4];
-                        if (k == 0) ld4(a.psiH_in + (size_t)ph * pitch + gx, psi);
-                        else ld4_rw(slotH + (size_t)ph * 128, psi);
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            float d = __fsub_rn(oE[q], pE[k + 1][q]);
-                            if (tf) d = __fsub_rn(d, einc);
-                            psi[q] = psi_new(b, c, psi[q], d);
-                            oX[q] = h_new_pml(pX[k][q], S, d, ik, psi[q]);
-                        }
-                        if (k == K - 1) {
-                            if (own) st4(a.psiH_out + (size_t)ph * pitch + gx, psi);
-                        } else {
-                            st4(slotH + (size_t)ph * 128, psi);
-                        }
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            float d = __fsub_rn(oE[q], pE[k + 1][q]);
-                            if (tf) d = __fsub_rn(d, einc);
-                            oX[q] = h_new(pX[k][q], S, d);
-                        }
-                    }
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) oX[q] = pX[k][q];
-                }
-                // ---- Hy^{n+1} at row r
-                const float eL = __shfl_up_sync(FULL, oE[3], 1);
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    oY[q] = h_new(pY[k][q], S, __fsub_rn(oE[q], q > 0 ? oE[q - 1] : eL));
-                // ---- monitor DFTs (Sec. 2.6) by the owning segment
-                if (own) {
-                    if (own_r && r == a.s.jr) {
-                        const double2 ph = a.s.phE[n];
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) dft_add(&a.s.dft[gx + q], oE[q], ph);
-                    }
-                    if (own_r && r == a.s.jr + 1) {
-                        const double2 ph = a.s.phH[n];
-#pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            dft_add(&a.s.dft[nx + gx + q], hx_avg(pX[k + 1][q], oX[q]), ph);
-                    }
-                    if (own_t && r == a.s.jt) {
-                        const double2 ph = a.s.phE[n];
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) dft_add(&a.s.dft[2 * nx + gx + q], oE[q], ph);
-                    }
-                    if (own_t && r == a.s.jt + 1) {
-                        const double2 ph = a.s.phH[n];
-#pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            dft_add(&a.s.dft[3 * nx + gx + q], hx_avg(pX[k + 1][q], oX[q]), ph);
+                        float d = __fsub_rn(oE[q], p.E[k + 1][q]);
+                        if (tf) d = __fsub_rn(d, einc);
+                        oX[q] = h_new(p.X[k][q], S, d);
                     }
                 }
             } else {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) { oE[q] = 0.f; oX[q] = 0.f; oY[q] = 0.f; }
+                for (int q = 0; q < 4; ++q) oX[q] = p.X[k][q];
             }
-            // level k now waits at row r+1; the new level-(k+1) row r flows up
+            const float eL = __shfl_up_sync(FULL, oE[3], 1);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                pE[k][q] = fE[q]; pX[k][q] = fX[q]; pY[k][q] = fY[q];
-                fE[q] = oE[q]; fX[q] = oX[q]; fY[q] = oY[q];
+            for (int q = 0; q < 4; ++q)
+                oY[q] = h_new(p.Y[k][q], S, __fsub_rn(oE[q], q > 0 ? oE[q - 1] : eL));
+            if (GENERAL && ln.own) {
+                if (ln.own_r && r == a.s.jr) {
+                    const double2 ph = a.s.phE[n];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) dft_add(&a.s.dft[ln.gx + q], oE[q], ph);
+                }
+                if (ln.own_r && r == a.s.jr + 1) {
+                    const double2 ph = a.s.phH[n];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        dft_add(&a.s.dft[ln.nx + ln.gx + q], hx_avg(p.X[k + 1][q], oX[q]), ph);
+                }
+                if (ln.own_t && r == a.s.jt) {
+                    const double2 ph = a.s.phE[n];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        dft_add(&a.s.dft[2 * ln.nx + ln.gx + q], oE[q], ph);
+                }
+                if (ln.own_t && r == a.s.jt + 1) {
+                    const double2 ph = a.s.phH[n];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        dft_add(&a.s.dft[3 * ln.nx + ln.gx + q], hx_avg(p.X[k + 1][q], oX[q]),
+                                ph);
+                }
             }
-            pL[k] = fL;
-            fL = cL;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) { oE[q] = 0.f; oX[q] = 0.f; oY[q] = 0.f; }
         }
+        // level k now waits at row r+1; the new level-(k+1) row r flows up
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            p.E[k][q] = fE[q]; p.X[k][q] = fX[q]; p.Y[k][q] = fY[q];
+            fE[q] = oE[q]; fX[q] = oX[q]; fY[q] = oY[q];
+        }
+        p.L[k] = fL;
+        fL = cL;
+    }
+}
+
+template <int K, bool U2>
+__global__ void __launch_bounds__(32) k_blocked(const BlockedArgs a, const int64_t n0) {
+    constexpr int H = ((K + 3) / 4) * 4;
+    __shared__ float2 s_coef[256];
+    for (int t = threadIdx.x; t < a.s.n_labels; t += blockDim.x) s_coef[t] = a.s.coef[t];
+    __syncwarp();
+
+    const int lane = threadIdx.x & 31;
+    const int task = blockIdx.x;                    // one warp per block and task
+    if (task >= a.n_tasks) return;
+    const int strip = task % a.n_strips;
+    const int seg = task / a.n_strips;
+    Lane ln;
+    ln.coef = s_coef;
+    ln.y0 = a.seg_y0[seg];
+    ln.y1 = a.seg_y0[seg + 1];
+    ln.nx = a.s.nx; ln.ny = a.s.ny; ln.P = a.s.P; ln.S = a.s.S;
+    const size_t pitch = (size_t)a.s.pitch;
+    const size_t lpitch = (size_t)a.s.lpitch;
+    const int xl = 4 * lane;                        // local column of the lane
+    const int xg_pre = strip * a.w_int - H + xl;    // global column before wrapping
+    ln.gx = ((xg_pre % ln.nx) + ln.nx) % ln.nx;     // nx % 4 == 0: 4 columns stay contiguous
+    ln.own = (xl >= H) && (xl < H + a.w_int) && (xg_pre < ln.nx);
+    ln.own_r = (a.s.jr >= ln.y0) && (a.s.jr < ln.y1);
+    ln.own_t = (a.s.jt >= ln.y0) && (a.s.jt < ln.y1);
+    float* slotE = a.slotE + (size_t)strip * 2 * ln.P * 128 + xl;
+    float* slotH = a.slotH + (size_t)strip * 2 * ln.P * 128 + xl;
+
+    Pipe<K> p;
+#pragma unroll
+    for (int k = 0; k <= K; ++k) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            p.E[k][q] = 0.f; p.X[k][q] = 0.f;
+            if (k < K) p.Y[k][q] = 0.f;
+        }
+        if (k < K) p.L[k] = 0u;
+    }
+
+    const int y0 = ln.y0, y1 = ln.y1, ny = ln.ny, P = ln.P;
+    const int t_begin = (y0 == 0) ? 0 : (y0 - K);
+    const int t_end = y1 + K;
+    // iterations whose rows t-K .. t-1 are all plain interior rows
+    const int fast_lo = max(max(y0 + K - 1, K + 1), P + K);
+    const int fast_hi = ny - P + 1;
+    const int sp[5] = {a.s.js, a.s.jr, a.s.jr + 1, a.s.jt, a.s.jt + 1};
+    auto is_fast = [&](int t) {
+        bool f = (t >= fast_lo) && (t < fast_hi);
+#pragma unroll
+        for (int s = 0; s < 5; ++s) f = f && ((unsigned)(t - sp[s] - 1) >= (unsigned)K);
+        return f;
+    };
+
+    // software pipeline: row t+1 is fetched while row t is processed
+    float nE[4], nX[4], nY[4];
+    uint32_t nL = 0u;
+    {
+        const size_t o = (size_t)t_begin * pitch + ln.gx;
+        ld4(a.ez_in + o, nE);
+        ld4(a.hx_in + o, nX);
+        ld4(a.hy_in + o, nY);
+        nL = __ldg(reinterpret_cast<const uint32_t*>(a.s.labels + (size_t)t_begin * lpitch + ln.gx));
+    }
+    auto iteration = [&](const int t, const bool fast) {
+        float fE[4], fX[4], fY[4];
+        uint32_t fL = nL;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { fE[q] = nE[q]; fX[q] = nX[q]; fY[q] = nY[q]; }
+        if (t + 1 < ny) {
+            const size_t o = (size_t)(t + 1) * pitch + ln.gx;
+            ld4(a.ez_in + o, nE);
+            ld4(a.hx_in + o, nX);
+            ld4(a.hy_in + o, nY);
+            nL = __ldg(reinterpret_cast<const uint32_t*>(a.s.labels + (size_t)(t + 1) * lpitch + ln.gx));
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) { nE[q] = 0.f; nX[q] = 0.f; nY[q] = 0.f; }
+            nL = 0u;
+        }
+        if (fast) advance<K, false>(p, fE, fX, fY, fL, t, a, ln, slotE, slotH, n0);
+        else advance<K, true>(p, fE, fX, fY, fL, t, a, ln, slotE, slotH, n0);
         const int ro = t - K;
-        if (own && ro >= y0 && ro < y1) {
-            const size_t o = (size_t)ro * pitch + gx;
+        if (ln.own && ro >= y0 && ro < y1) {
+            const size_t o = (size_t)ro * pitch + ln.gx;
             st4(a.ez_out + o, fE);
             st4(a.hx_out + o, fX);
             st4(a.hy_out + o, fY);
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) { pE[K][q] = fE[q]; pX[K][q] = fX[q]; }
+        for (int q = 0; q < 4; ++q) { p.E[K][q] = fE[q]; p.X[K][q] = fX[q]; }
+    };
+    int t = t_begin;
+#pragma unroll 1
+    while (t < t_end) {
+        if (U2 && t + 1 < t_end && is_fast(t) && is_fast(t + 1)) {
+            iteration(t, true);
+            iteration(t + 1, true);
+            t += 2;
+        } else {
+            if (is_fast(t)) iteration(t, true);
+            else iteration(t, false);
+            t += 1;
+        }
     }
+}
+
+template <int K, bool U2>
+static int occupancy_warps() {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_blocked<K, U2>, 32, 0) != cudaSuccess)
+        return 0;
+    return b;
 }
 
 int blocked_max_K() { return 8; }
 
-bool launch_blocked(const BlockedArgs& a, int K, int64_t n0, cudaStream_t st) {
-    const int warps = 4;
-    const unsigned grid = (unsigned)((a.n_tasks + warps - 1) / warps);
+#define FDTD_BLOCKED_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8)
+
+int blocked_warps_per_sm(int K, int variant) {
     switch (K) {
-        case 1: k_blocked<1><<<grid, 32 * warps, 0, st>>>(a, n0); break;
-        case 2: k_blocked<2><<<grid, 32 * warps, 0, st>>>(a, n0); break;
-        case 3: k_blocked<3><<<grid, 32 * warps, 0, st>>>(a, n0); break;
-        case 4: k_blocked<4><<<grid, 32 * warps, 0, st>>>(a, n0); break;
-        case 5: k_blocked<5><<<grid, 32 * warps, 0, st>>>(a, n0); break;
-        case 6: k_blocked<6><<<grid, 32 * warps, 0, st>>>(a, n0); break;
-        case 7: k_blocked<7><<<grid, 32 * warps, 0, st>>>(a, n0); break;
-        case 8: k_blocked<8><<<grid, 32 * warps, 0, st>>>(a, n0); break;
+#define X(k) case k: return variant ? occupancy_warps<k, true>() : occupancy_warps<k, false>();
+        FDTD_BLOCKED_CASES(X)
+#undef X
+        default: return 0;
+    }
+}
+
+bool launch_blocked(const BlockedArgs& a, int K, int variant, int64_t n0, cudaStream_t st) {
+    const unsigned grid = (unsigned)a.n_tasks;
+    switch (K) {
+#define X(k)                                                                  \
+    case k:                                                                   \
+        if (variant) k_blocked<k, true><<<grid, 32, 0, st>>>(a, n0);          \
+        else k_blocked<k, false><<<grid, 32, 0, st>>>(a, n0);                 \
+        break;
+        FDTD_BLOCKED_CASES(X)
+#undef X
         default: return false;
     }
     return true;

@@ -39,6 +39,7 @@ struct BlockPlan {
     int n_strips = 0;
     int n_segs = 0;
     int seg_rows = 0;
+    int variant = -1;
     int* d_seg_y0 = nullptr;  // n_segs + 1 row boundaries
 };
 
@@ -76,8 +77,9 @@ void launch_unpack(const float* src, int nx, int ny, float scale, float* dst, in
 void launch_scale_double(double* p, int64_t n, double scale, cudaStream_t st);
 void launch_check_finite(const float* p, int pitch, int nx, int ny, int* flag,
                          cudaStream_t st);
-bool launch_blocked(const BlockedArgs& a, int K, int64_t n0, cudaStream_t st);
+bool launch_blocked(const BlockedArgs& a, int K, int variant, int64_t n0, cudaStream_t st);
 int blocked_max_K();
+int blocked_warps_per_sm(int K, int variant);
 
 }  // namespace fdtd
 
@@ -122,7 +124,7 @@ struct fdtd_handle {
     // blocked-kernel plans per depth
     std::vector<fdtd::BlockPlan> plans;
     // options
-    int opt_kernel = 0, opt_block = 8, opt_seg = 0, opt_timing = 0;
+    int opt_kernel = 0, opt_block = 8, opt_seg = 0, opt_timing = 0, opt_variant = 0;
     int64_t opt_watchdog = 0;
     // stats
     int64_t n = 0;

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "libfdtd.so")
 FDTD_OK, FDTD_EINVAL, FDTD_ENOMEM, FDTD_ECUDA = 0, -1, -2, -3
 FDTD_EUNSTABLE, FDTD_ETIMEOUT, FDTD_ESTATE = -4, -5, -6
 FDTD_OPT_KERNEL, FDTD_OPT_BLOCK_STEPS, FDTD_OPT_SEG_ROWS = 1, 2, 3
-FDTD_OPT_TIMING, FDTD_OPT_WATCHDOG = 4, 5
+FDTD_OPT_TIMING, FDTD_OPT_WATCHDOG, FDTD_OPT_VARIANT = 4, 5, 6
 KERNEL_AUTO, KERNEL_NAIVE, KERNEL_BLOCKED = 0, 1, 2
 
 

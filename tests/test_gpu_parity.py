@@ -86,14 +86,16 @@ def test_config1b_fields_and_rt(fd, ref_c1b, kernel, K):
     _run_and_compare(fd, spec, tr, rt, kernel, K)
 
 
-@pytest.mark.parametrize("K,seg", [(8, None), (8, 25), (7, 40), (5, 23), (4, 31), (2, 19),
-                                   (1, 17), (6, 200)])
-def test_blocked_is_bitwise_equal_to_naive(fd, K, seg):
+@pytest.mark.parametrize("K,seg,variant", [(8, None, 1), (8, None, 0), (8, 25, 1), (7, 40, 0),
+                                           (7, 40, 1), (5, 23, 1), (4, 31, 0), (2, 19, 1),
+                                           (1, 17, 1), (6, 200, 0), (6, 33, 1), (3, 29, 1)])
+def test_blocked_is_bitwise_equal_to_naive(fd, K, seg, variant):
     spec = config_c1b(steps=411)
     with fd.Simulation(spec, kernel=1) as a:
         a.run(411)
         fa, da = a.fields(), a.dft()
     with fd.Simulation(spec, kernel=2, block_steps=K, seg_rows=seg) as b:
+        fd.fdtd_set_option(b.h, fd.FDTD_OPT_VARIANT, variant)
         b.run(200)
         b.run(211)
         fb, db = b.fields(), b.dft()
