@@ -97,9 +97,9 @@ def default_cpml(dx: float, lambda0: float, order: float = 3.0) -> dict:
 def leaf_materials(lambda_m: float, n_labels: int = 6) -> np.ndarray:
     """(n, kappa) per leaf label at wavelength lambda (metres).
 
-    Cuticle n = 1.45 and cell wall n = 1.52 follow Sec. 2.7; cytoplasm,
+    Cuticle n = 1.45 and cell wall n = 1.52 follow Sec. 2.8; cytoplasm,
     vacuole and the melanised hypha use closed-form kappa(lambda) curves that
-    stand in for the pigment, water and melanin data of Sec. 2.7 and Sec. 4.2.
+    stand in for the pigment, water and melanin data of Sec. 2.8 and Sec. 4.2.
     """
     lam = lambda_m * 1e9
     k_cyt = 0.02 * (math.exp(-((lam - 430.0) / 25.0) ** 2)

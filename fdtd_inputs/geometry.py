@@ -1,11 +1,11 @@
 """Seeded label maps (segmented cross-sections) for the workloads.
 
 The paper builds its label maps from hand-segmented micrographs with randomly
-inserted chloroplast ellipses (Sec. 2.6). The micrographs are not available,
+inserted chloroplast ellipses (Sec. 2.7). The micrographs are not available,
 so these generators draw synthetic tissue of the same kind from a seed:
 layered cuticle / epidermis / palisade / spongy mesophyll with 0.3 um cell
 walls, a 1 um cytoplasm lining, vacuoles, chloroplast ellipses sampled as in
-Sec. 2.6 (a = 0.8 + 0.2 (2 r1 - 1) um, b = a (1 + (r2 - 0.5)), theta uniform),
+Sec. 2.7 (a = 0.8 + 0.2 (2 r1 - 1) um, b = a (1 + (r2 - 0.5)), theta uniform),
 and optional melanised hyphae (Sec. 4.2). All maps are uint8, shape (ny, nx),
 row 0 at the top, periodic in x.
 """
@@ -153,7 +153,7 @@ def _jittered_seeds(rng, nx, r0, r1, spacing_x, spacing_y, jitter=0.35):
 
 def _add_chloroplasts(rng, lab, depth, r0, r1, per_um, frac=0.2, l_chl_um=2.0,
                       t_wall=0.0):
-    """Insert rotated chloroplast ellipses (Sec. 2.6) labelled cytoplasm into the
+    """Insert rotated chloroplast ellipses (Sec. 2.7) labelled cytoplasm into the
     cell interiors of rows [r0, r1) until they cover `frac` of the non-air
     mesophyll area; centres lie within l_chl of a cell wall."""
     ny_b, nx = r1 - r0, lab.shape[1]
