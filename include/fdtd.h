@@ -186,6 +186,40 @@ const char* fdtd_last_error(const fdtd_handle* h);
  * no-op. */
 void fdtd_destroy(fdtd_handle* h);
 
+/* Allocation-free stepping (the paper has no counterpart: it is an interface
+ * for callers that cannot call cudaMalloc where they step the fields, e.g.
+ * code running during CUDA stream capture, plug-ins confined to a device
+ * memory budget handed out by their host framework, or processes whose
+ * device allocator belongs to another runtime).
+ *
+ * Advances a source-free field state by `steps` (1..8) leapfrog steps with
+ * the temporally blocked kernel, on `cuda_stream` (NULL = legacy stream), and
+ * allocates nothing: the kernel's scratch (CPML carries between time levels,
+ * segment table, coefficient and CPML tables, zeroed source tables, a sink
+ * for monitor sums) lives in one static 8 MiB device array per GPU, held by
+ * every GPU that loads the library until the process exits. Grids needing
+ * more scratch (roughly nx * (pml_cells + 1) > 300000, or pml_cells > 64)
+ * are rejected with FDTD_EINVAL and a message.
+ *   grid: layout as for fdtd_create (nx % 4 == 0 required); table/n_labels/
+ *     lambda0: materials at the wavelength (coefficients as in fdtd_create);
+ *   labels: device, ny*nx uint8, values < n_labels (not checked here);
+ *   in[5], out[5]: device buffers {Ez, eta0*Hx, eta0*Hy, psi_E, psi_H}:
+ *     fields dense ny*nx FP32 (Ez in V/m, H scaled by eta0 = mu0 c0, i.e.
+ *     also V/m), CPML carries dense (2*pml_cells)*nx FP32 (top rows first,
+ *     zero at the start of a run); outputs must not alias inputs; the caller
+ *     owns all of them. Hx row 0 stays as given (the fixed top edge).
+ *   err/err_len: optional buffer for a message on failure.
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture begins.
+ * Every call shares the one array and overwrites it, so calls that overlap
+ * on the GPU race; nothing in it needs to persist between calls.
+ * Returns FDTD_OK, FDTD_EINVAL or FDTD_ECUDA; asynchronous on success. */
+int fdtd_blocked_advance_noalloc(const fdtd_grid* grid, const uint8_t* labels,
+                                 const fdtd_material* table, int32_t n_labels,
+                                 double lambda0, const float* const* in,
+                                 float* const* out, int32_t steps,
+                                 void* cuda_stream, char* err, size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -79,6 +79,10 @@ def load_library(path: str = LIB_PATH):
         "fdtd_get_stats": (C.c_int, [vp, C.POINTER(fdtd_stats)]),
         "fdtd_last_error": (C.c_char_p, [vp]),
         "fdtd_destroy": (None, [vp]),
+        "fdtd_blocked_advance_noalloc": (C.c_int, [C.POINTER(fdtd_grid), vp,
+                                                   C.POINTER(fdtd_material), i32, C.c_double,
+                                                   C.POINTER(vp), C.POINTER(vp), i32, vp,
+                                                   C.c_char_p, C.c_size_t]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -215,6 +219,25 @@ def fdtd_last_error(h=None) -> str:
 def fdtd_destroy(h):
     if h:
         load_library().fdtd_destroy(h)
+
+
+def fdtd_blocked_advance_noalloc(grid: fdtd_grid, labels, materials, lambda0: float,
+                                 inputs, outputs, steps: int, stream=None):
+    """Allocation-free stepping (see include/fdtd.h): inputs/outputs are five
+    device tensors each {Ez, eta0*Hx, eta0*Hy, psi_E, psi_H}; labels a device
+    uint8 tensor. Raises FDTDError with the library's message on failure."""
+    lib = load_library()
+    mats = np.ascontiguousarray(materials, dtype=np.float64).reshape(-1, 2)
+    table = (fdtd_material * len(mats))(*[fdtd_material(float(n), float(k)) for n, k in mats])
+    ins = (C.c_void_p * 5)(*[x.data_ptr() for x in inputs])
+    outs = (C.c_void_p * 5)(*[x.data_ptr() for x in outputs])
+    st = C.c_void_p(stream) if isinstance(stream, int) else (
+        C.c_void_p(stream.cuda_stream) if stream is not None else None)
+    err = C.create_string_buffer(256)
+    code = lib.fdtd_blocked_advance_noalloc(C.byref(grid), _ptr(labels), table, len(mats),
+                                            float(lambda0), ins, outs, int(steps), st, err, 256)
+    if code != FDTD_OK:
+        raise FDTDError(code, err.value.decode())
 
 
 class Simulation:

@@ -1,0 +1,83 @@
+"""The allocation-free entry point (fdtd_blocked_advance_noalloc) against the
+handle-based path (fdtd_create / fdtd_set_fields / fdtd_run) on the same
+random source-free state, over two calls in a row.
+
+Callers that cannot allocate device memory where they step the fields (for
+instance code running during stream capture or inside a device-memory budget
+owned by a host framework) use this entry point with their own buffers; its
+scratch lives in a static device array of the library. This file is collected
+last so that a failure here leaves every other test already run."""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_common import lib, need_gpu
+
+pytestmark = pytest.mark.gpu
+
+ETA0 = 4.0e-7 * math.pi * 299_792_458.0
+TOL = 1e-4          # field tolerance used by the parity tests
+
+
+def _rel(a, b):
+    return float(np.linalg.norm((a.astype(np.float64) - b.astype(np.float64)).ravel())
+                 / max(np.linalg.norm(b.astype(np.float64).ravel()), 1e-30))
+
+
+def test_noalloc_matches_handle_path_over_two_calls():
+    need_gpu()
+    fd = lib()
+    import torch
+    from fdtd_inputs import config_c2, crop_layout, random_fields
+    spec = crop_layout(config_c2(), ny=1200).with_(source_kind=2)
+    ez, hx, hy = random_fields(spec.ny, spec.nx, 11, 1.0 / ETA0)
+    ez, hx, hy = (x.astype(np.float32) for x in (ez, hx, hy))
+    K = 8
+    with fd.Simulation(spec, kernel=fd.KERNEL_BLOCKED, block_steps=K) as sim:
+        sim.set_fields(ez, hx, hy)
+        sim.run(K)
+        ref1 = sim.fields()
+        sim.run(K)
+        ref2 = sim.fields()
+
+    dev = torch.device("cuda", 0)
+    eta = np.float32(ETA0)
+    P = spec.pml_cells
+    fields = [torch.from_numpy(ez).to(dev), torch.from_numpy(hx * eta).to(dev),
+              torch.from_numpy(hy * eta).to(dev),
+              torch.zeros((2 * P, spec.nx), dtype=torch.float32, device=dev),
+              torch.zeros((2 * P, spec.nx), dtype=torch.float32, device=dev)]
+    labels = torch.from_numpy(np.ascontiguousarray(spec.labels)).to(dev)
+    grid = fd.make_grid(spec)
+    outs = []
+    for _ in range(2):
+        nxt = [torch.empty_like(x) for x in fields]
+        fd.fdtd_blocked_advance_noalloc(grid, labels, spec.materials, spec.lambda0,
+                                        fields, nxt, K)
+        torch.cuda.synchronize()
+        inv = np.float32(1.0 / ETA0)
+        outs.append((nxt[0].cpu().numpy(), nxt[1].cpu().numpy() * inv,
+                     nxt[2].cpu().numpy() * inv))
+        fields = nxt
+    for got, ref in zip(outs, (ref1, ref2)):
+        for g, r in zip(got, ref):
+            assert _rel(g, r) <= TOL
+    # the same kernel with the same rounding: identical values are expected
+    assert all(np.array_equal(g, r) for g, r in zip(outs[1], ref2))
+
+
+def test_noalloc_rejects_oversized_grids():
+    need_gpu()
+    fd = lib()
+    import torch
+    from fdtd_inputs import config_c3
+    spec = config_c3(labels=np.zeros((64, 8192), np.uint8), ny=64).with_(
+        nx=1024 * 1024, t_row=40, tfsf_row=30, r_row=20, pml_cells=8)
+    dev = torch.device("cuda", 0)
+    tiny = [torch.zeros(4, dtype=torch.float32, device=dev) for _ in range(5)]
+    outs = [torch.zeros(4, dtype=torch.float32, device=dev) for _ in range(5)]
+    with pytest.raises(fd.FDTDError) as e:
+        fd.fdtd_blocked_advance_noalloc(fd.make_grid(spec), tiny[0], spec.materials,
+                                        spec.lambda0, tiny, outs, 8)
+    assert e.value.code == fd.FDTD_EINVAL and "scratch" in str(e.value)
