@@ -116,6 +116,7 @@ typedef struct fdtd_stats {
 #define FDTD_OPT_TIMING 4      /* 1: time stencil launches with CUDA events */
 #define FDTD_OPT_WATCHDOG 5    /* check fields for non-finite values every N steps (0 off) */
 #define FDTD_OPT_VARIANT 6     /* blocked-kernel code shape: 0 one row per loop trip (default), 1 two */
+#define FDTD_OPT_GRAPH 7       /* batches: replay captured CUDA graphs of launch chunks (default 1) */
 
 /* Create a simulation. grid, labels (ny*nx uint8, values < n_labels), table
  * (n_labels entries, n > k >= 0) and source are copied; the caller keeps
@@ -146,7 +147,9 @@ int fdtd_synchronize(fdtd_handle* h);
 
 /* Reflectance and transmittance at lambda0 from the DFTs accumulated so far
  * (Sec. 2.6, Poynting form): R = P_up(r_row)/P_inc, T = P_down(t_row)/P_inc,
- * P_inc = nx * P_down(t_row) of the empty-domain run. Synchronises. */
+ * P_inc = nx * P_down(t_row) of the empty-domain run. Synchronises. Before
+ * the incident pulse has reached t_row, P_inc is 0 and R, T are not finite
+ * (IEEE division); fdtd_flux_raw gives the powers themselves. */
 int fdtd_flux(fdtd_handle* h, double* R, double* T);
 
 /* The three fluxes behind R and T in W/m (per unit z length):
@@ -185,6 +188,38 @@ const char* fdtd_last_error(const fdtd_handle* h);
 /* Release the handle and its device memory (waits for its work). NULL is a
  * no-op. */
 void fdtd_destroy(fdtd_handle* h);
+
+/* Pick the blocked kernel's steps per launch, code shape and segment height
+ * for this handle's grid by timing `trial_launches` launches of each
+ * candidate on the current state. The trial launches write only scratch
+ * (the other ping-pong buffers and a dummy monitor sink), so the simulation
+ * state is unchanged. The choice is remembered per (nx, ny, pml_cells,
+ * device) for later handles. Synchronises. */
+int fdtd_autotune(fdtd_handle* h, int32_t trial_launches);
+
+/* Batched runs of independent simulations (the paper runs one simulation
+ * per wavelength, polarisation and slice, Sec. 2.2 and Sec. 4; here they
+ * share the GPU). A batch groups existing handles (same device, nx % 4 == 0
+ * each; the handles must outlive the batch). fdtd_batch_run advances every
+ * handle by `steps` in lockstep: one blocked-kernel launch per K steps
+ * covers the warp tasks of all simulations, the empty-domain runs go as one
+ * launch on a side stream, and full chunks of launches are captured once
+ * into a CUDA graph and replayed (FDTD_OPT_GRAPH). The results are exactly
+ * those of running each handle alone; read them with fdtd_flux etc. on each
+ * handle. Work is ordered after earlier work on every handle's streams and
+ * later work on them waits for the batch. Options: FDTD_OPT_BLOCK_STEPS,
+ * FDTD_OPT_SEG_ROWS, FDTD_OPT_VARIANT, FDTD_OPT_TIMING, FDTD_OPT_GRAPH.
+ * fdtd_batch_autotune times candidate launch shapes on the whole batch like
+ * fdtd_autotune (state unchanged). Stats: reserved = 1 when a graph is in use.
+ * Errors of fdtd_batch_create are reported by fdtd_batch_last_error(NULL). */
+typedef struct fdtd_batch fdtd_batch;
+int fdtd_batch_create(fdtd_handle* const* hs, int32_t n, fdtd_batch** out);
+int fdtd_batch_set_option(fdtd_batch* b, int32_t option, int64_t value);
+int fdtd_batch_autotune(fdtd_batch* b, int32_t trial_launches);
+int fdtd_batch_run(fdtd_batch* b, int64_t steps);
+int fdtd_batch_get_stats(fdtd_batch* b, fdtd_stats* out);
+const char* fdtd_batch_last_error(const fdtd_batch* b);
+void fdtd_batch_destroy(fdtd_batch* b);
 
 /* Allocation-free stepping (the paper has no counterpart: it is an interface
  * for callers that cannot call cudaMalloc where they step the fields, e.g.

@@ -14,7 +14,7 @@
 
 using namespace fdtd;
 
-namespace {
+namespace fdtd {
 
 constexpr double kC0 = 299792458.0;
 constexpr double kPi = 3.14159265358979323846;
@@ -24,10 +24,6 @@ const double kEta0 = kMu0 * kC0;
 constexpr int64_t kChunk = 1024;   // steps per incident-table chunk
 
 thread_local std::string g_create_err;
-
-struct Fail {
-    int code;
-};
 
 #define CK(call)                                                                   \
     do {                                                                           \
@@ -152,6 +148,22 @@ int sm_count(fdtd_handle* h) {
     return v;
 }
 
+// Row boundaries of the warp-task segments: `seg` rows each; the last
+// segment absorbs a remainder shorter than min_seg; no boundary may fall
+// just below a monitor row (the owning segment needs the row below it).
+std::vector<int> segment_bounds(const fdtd_grid& g, int seg, int min_seg) {
+    std::vector<int> b{0};
+    int pos = seg;
+    while (pos < g.ny) {
+        if (pos == g.r_row + 1 || pos == g.t_row + 1) ++pos;
+        if (g.ny - pos < min_seg) break;
+        b.push_back(pos);
+        pos += seg;
+    }
+    b.push_back(g.ny);
+    return b;
+}
+
 // Segment plan of the blocked kernel for depth K (see blocked.cu). One warp
 // task per (strip, segment); with W warps resident on the whole GPU, the
 // segment count is chosen to minimise waves x (rows per segment + 2K), the
@@ -193,15 +205,7 @@ BlockPlan& get_plan(fdtd_handle* h, int K) {
         }
     }
     seg = std::max(seg, min_seg);
-    std::vector<int> b{0};
-    int pos = seg;
-    while (pos < g.ny) {
-        if (pos == g.r_row + 1 || pos == g.t_row + 1) ++pos;
-        if (g.ny - pos < min_seg) break;
-        b.push_back(pos);
-        pos += seg;
-    }
-    b.push_back(g.ny);
+    const std::vector<int> b = segment_bounds(g, seg, min_seg);
     p.n_segs = (int)b.size() - 1;
     p.seg_rows = seg;
     CK(cudaMalloc(&p.d_seg_y0, b.size() * sizeof(int)));
@@ -344,7 +348,7 @@ __global__ void k_max_label(const uint8_t* lab, int lpitch, int nx, int ny, int*
     if (i < nx) atomicMax(out, (int)lab[(size_t)j * lpitch + i]);
 }
 
-}  // namespace
+}  // namespace fdtd
 
 // --------------------------------------------------------------------------
 // incident-wave generator

@@ -196,16 +196,12 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
     }
 }
 
+// One warp task: strip `task % n_strips` of segment `task / n_strips`.
 template <int K, bool U2>
-__global__ void __launch_bounds__(32) k_blocked(const BlockedArgs a, const int64_t n0) {
+__device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float2* s_coef,
+                                             const int task, const int64_t n0) {
     constexpr int H = ((K + 3) / 4) * 4;
-    __shared__ float2 s_coef[256];
-    for (int t = threadIdx.x; t < a.s.n_labels; t += blockDim.x) s_coef[t] = a.s.coef[t];
-    __syncwarp();
-
     const int lane = threadIdx.x & 31;
-    const int task = blockIdx.x;                    // one warp per block and task
-    if (task >= a.n_tasks) return;
     const int strip = task % a.n_strips;
     const int seg = task / a.n_strips;
     Lane ln;
@@ -303,6 +299,41 @@ __global__ void __launch_bounds__(32) k_blocked(const BlockedArgs a, const int64
 }
 
 template <int K, bool U2>
+__global__ void __launch_bounds__(32) k_blocked(const BlockedArgs a, const int64_t n0) {
+    __shared__ float2 s_coef[256];
+    for (int t = threadIdx.x; t < a.s.n_labels; t += blockDim.x) s_coef[t] = a.s.coef[t];
+    __syncwarp();
+    if ((int)blockIdx.x >= a.n_tasks) return;       // one warp per block and task
+    blocked_task<K, U2>(a, s_coef, blockIdx.x, n0);
+}
+
+// Many independent simulations in one launch: the grid covers the union of
+// their warp tasks. Each block finds its simulation, copies that
+// simulation's arguments (ping-pong orientation `parity`) to shared memory
+// and runs the same task body. The absolute step of the launch is
+// n_base(sim) + *step_base + step_off, so a captured chunk of launches can be
+// replayed with a new *step_base.
+template <int K, bool U2>
+__global__ void __launch_bounds__(32) k_blocked_batch(const BatchArgs b, const int step_off,
+                                                      const int parity) {
+    __shared__ float2 s_coef[256];
+    __shared__ __align__(16) unsigned char s_raw[sizeof(BlockedArgs)];
+    const int task = blockIdx.x;
+    if (task >= b.n_tasks) return;
+    const int sim = b.task_sim[task];
+    const BlockedArgs* src = b.sims + (size_t)parity * b.n_sims + sim;
+    const int* w = reinterpret_cast<const int*>(src);
+    int* d = reinterpret_cast<int*>(s_raw);
+    for (int q = threadIdx.x; q < (int)(sizeof(BlockedArgs) / sizeof(int)); q += 32) d[q] = w[q];
+    __syncwarp();
+    const BlockedArgs& a = *reinterpret_cast<const BlockedArgs*>(s_raw);
+    for (int t = threadIdx.x; t < a.s.n_labels; t += 32) s_coef[t] = a.s.coef[t];
+    __syncwarp();
+    const int64_t n0 = a.n_base + *b.step_base + step_off;
+    blocked_task<K, U2>(a, s_coef, task - b.first_task[sim], n0);
+}
+
+template <int K, bool U2>
 static int occupancy_warps() {
     int b = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_blocked<K, U2>, 32, 0) != cudaSuccess)
@@ -321,6 +352,22 @@ int blocked_warps_per_sm(int K, int variant) {
 #undef X
         default: return 0;
     }
+}
+
+bool launch_blocked_batch(const BatchArgs& b, int K, int variant, int step_off, int parity,
+                          cudaStream_t st) {
+    const unsigned grid = (unsigned)b.n_tasks;
+    switch (K) {
+#define X(k)                                                                            \
+    case k:                                                                             \
+        if (variant) k_blocked_batch<k, true><<<grid, 32, 0, st>>>(b, step_off, parity); \
+        else k_blocked_batch<k, false><<<grid, 32, 0, st>>>(b, step_off, parity);        \
+        break;
+        FDTD_BLOCKED_CASES(X)
+#undef X
+        default: return false;
+    }
+    return true;
 }
 
 bool launch_blocked(const BlockedArgs& a, int K, int variant, int64_t n0, cudaStream_t st) {

@@ -52,9 +52,20 @@ struct BlockedArgs {
     float* slotE; float* slotH;   // per-strip CPML carries [n_strips][2][P][128]
     const int* seg_y0;
     int n_strips, n_tasks, w_int;
+    int64_t n_base;               // batch launches: absolute step of the batch start
+};
+
+// Arguments of the batched blocked kernel (all simulations in one launch).
+struct BatchArgs {
+    const BlockedArgs* sims;      // [2][n_sims]: ping-pong orientation 0 and 1
+    const int* task_sim;          // simulation of each task
+    const int* first_task;        // first task of each simulation
+    const int64_t* step_base;     // device: step offset of the current chunk
+    int n_sims, n_tasks;
 };
 
 struct TwinArgs {
+    int64_t n_base;       // batch launches: absolute step of the batch start
     int ny, P, js, jr, jt;
     float S, ca, cb;      // air coefficients
     const float* pml_e; const float* pml_h;
@@ -64,6 +75,7 @@ struct TwinArgs {
     double2* dft;         // [4]: Ez(jr), Hx(jr), Ez(jt), Hx(jt)
 };
 
+struct BlockPlan;
 // launchers (kernels.cu, blocked.cu)
 void launch_naive_step(const StepArgs& a, float* ez, float* hx, float* hy,
                        float* psiE, float* psiH, int64_t n, cudaStream_t st);
@@ -78,8 +90,25 @@ void launch_scale_double(double* p, int64_t n, double scale, cudaStream_t st);
 void launch_check_finite(const float* p, int pitch, int nx, int ny, int* flag,
                          cudaStream_t st);
 bool launch_blocked(const BlockedArgs& a, int K, int variant, int64_t n0, cudaStream_t st);
+bool launch_blocked_batch(const BatchArgs& b, int K, int variant, int step_off, int parity,
+                          cudaStream_t st);
+void configure_twin_batch();
+void launch_twin_batch(const TwinArgs* tws, int n, int max_ny, int max_P,
+                       const int64_t* step_base, int steps, cudaStream_t st);
 int blocked_max_K();
 int blocked_warps_per_sm(int K, int variant);
+
+// host helpers shared by the handle, batch and tuning code (api.cu); they
+// throw Fail with the handle's error message set
+struct Fail {
+    int code;
+};
+StepArgs step_args(fdtd_handle* h);
+void ensure_tables(fdtd_handle* h, int64_t n_end);
+void produce_tables(fdtd_handle* h, int64_t upto);
+int sm_count(fdtd_handle* h);
+void sync_all(fdtd_handle* h);
+std::vector<int> segment_bounds(const fdtd_grid& g, int seg, int min_seg);
 
 }  // namespace fdtd
 

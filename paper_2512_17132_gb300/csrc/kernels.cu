@@ -83,7 +83,7 @@ void launch_naive_step(const StepArgs& a, float* ez, float* hx, float* hy, float
 // Empty-domain reference run: one column of air (an x-uniform field has
 // Hy = 0 and needs a single column), same rows, CPML, source and monitors.
 // One block advances `steps` steps; the column lives in global memory.
-__global__ void __launch_bounds__(1024) k_twin(TwinArgs a, int64_t n0, int steps) {
+__device__ __forceinline__ void twin_column_global(const TwinArgs& a, int64_t n0, int steps) {
     const int ny = a.ny;
     for (int s = 0; s < steps; ++s) {
         const int64_t n = n0 + s;
@@ -127,8 +127,131 @@ __global__ void __launch_bounds__(1024) k_twin(TwinArgs a, int64_t n0, int steps
     }
 }
 
+__global__ void __launch_bounds__(1024) k_twin(TwinArgs a, int64_t n0, int steps) {
+    twin_column_global(a, n0, steps);
+}
+
+// The same column kept in shared memory for the whole launch (when it fits):
+// identical arithmetic and order, the DFT sums carried in registers of
+// thread 0 and written back at the end.
+__device__ __forceinline__ void twin_column_smem(const TwinArgs& a, int64_t n0, int steps,
+                                                 float* sm) {
+    const int ny = a.ny, P2 = 2 * a.P;
+    float* ez = sm;
+    float* hx = sm + ny;
+    float* pE = hx + ny;
+    float* pH = pE + P2;
+    for (int j = threadIdx.x; j < ny; j += blockDim.x) { ez[j] = a.ez[j]; hx[j] = a.hx[j]; }
+    for (int j = threadIdx.x; j < P2; j += blockDim.x) { pE[j] = a.psiE[j]; pH[j] = a.psiH[j]; }
+    double2 d0 = a.dft[0], d1 = a.dft[1], d2 = a.dft[2], d3 = a.dft[3];
+    __syncthreads();
+    for (int s = 0; s < steps; ++s) {
+        const int64_t n = n0 + s;
+        const float hinc = a.hinc[n], einc = a.einc[n];
+        for (int j = threadIdx.x; j < ny; j += blockDim.x) {
+            const float hxb = (j + 1 < ny) ? hx[j + 1] : 0.0f;
+            float dhx = __fsub_rn(hxb, hx[j]);
+            if (j == a.js) dhx = __fsub_rn(dhx, hinc);
+            const float e = ez[j];
+            const int pj = pml_e_index(j, ny, a.P);
+            if (pj >= 0) {
+                const float p = psi_new(a.pml_e[pj], a.pml_e[2 * a.P + pj], pE[pj], dhx);
+                pE[pj] = p;
+                ez[j] = ez_new_pml(a.ca, a.cb, e, 0.0f, dhx, a.pml_e[4 * a.P + pj], p);
+            } else {
+                ez[j] = ez_new(a.ca, a.cb, e, 0.0f, dhx);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            dft_add(&d0, ez[a.jr], a.phE[n]);
+            dft_add(&d2, ez[a.jt], a.phE[n]);
+        }
+        for (int j = threadIdx.x + 1; j < ny; j += blockDim.x) {
+            float d = __fsub_rn(ez[j], ez[j - 1]);
+            if (j == a.js) d = __fsub_rn(d, einc);
+            const int pj = pml_h_index(j, ny, a.P);
+            if (pj >= 0) {
+                const float p = psi_new(a.pml_h[pj], a.pml_h[2 * a.P + pj], pH[pj], d);
+                pH[pj] = p;
+                hx[j] = h_new_pml(hx[j], a.S, d, a.pml_h[4 * a.P + pj], p);
+            } else {
+                hx[j] = h_new(hx[j], a.S, d);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            dft_add(&d1, hx_avg(hx[a.jr], hx[a.jr + 1]), a.phH[n]);
+            dft_add(&d3, hx_avg(hx[a.jt], hx[a.jt + 1]), a.phH[n]);
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < ny; j += blockDim.x) { a.ez[j] = ez[j]; a.hx[j] = hx[j]; }
+    for (int j = threadIdx.x; j < P2; j += blockDim.x) { a.psiE[j] = pE[j]; a.psiH[j] = pH[j]; }
+    if (threadIdx.x == 0) { a.dft[0] = d0; a.dft[1] = d1; a.dft[2] = d2; a.dft[3] = d3; }
+}
+
+__global__ void __launch_bounds__(512) k_twin_smem(TwinArgs a, int64_t n0, int steps) {
+    extern __shared__ float sm[];
+    twin_column_smem(a, n0, steps, sm);
+}
+
+// One block per simulation of a batch; steps start at n_base + *step_base.
+__global__ void __launch_bounds__(512) k_twin_batch_smem(const TwinArgs* tws,
+                                                         const int64_t* step_base, int steps) {
+    extern __shared__ float sm[];
+    const TwinArgs a = tws[blockIdx.x];
+    twin_column_smem(a, a.n_base + *step_base, steps, sm);
+}
+
+__global__ void __launch_bounds__(1024) k_twin_batch_global(const TwinArgs* tws,
+                                                            const int64_t* step_base, int steps) {
+    const TwinArgs a = tws[blockIdx.x];
+    twin_column_global(a, a.n_base + *step_base, steps);
+}
+
 void launch_twin(const TwinArgs& a, int64_t n0, int steps, cudaStream_t st) {
-    k_twin<<<1, 1024, 0, st>>>(a, n0, steps);
+    constexpr size_t kMaxSmem = 200 * 1024;
+    const size_t smem = (size_t)(2 * a.ny + 4 * a.P) * sizeof(float);
+    if (smem <= kMaxSmem) {
+        static bool configured[64] = {};   // the opt-in is per function and device
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev < 0 || dev >= 64 || !configured[dev]) {
+            cudaFuncSetAttribute(k_twin_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kMaxSmem);
+            if (dev >= 0 && dev < 64) configured[dev] = true;
+        }
+        k_twin_smem<<<1, 512, smem, st>>>(a, n0, steps);
+    } else {
+        k_twin<<<1, 1024, 0, st>>>(a, n0, steps);
+    }
+}
+
+// Shared-memory opt-in of the batched column kernel on the current device;
+// done before any stream capture that contains the kernel.
+void configure_twin_batch() {
+    cudaFuncSetAttribute(k_twin_batch_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+}
+
+void launch_twin_batch(const TwinArgs* tws, int n, int max_ny, int max_P,
+                       const int64_t* step_base, int steps, cudaStream_t st) {
+    constexpr size_t kMaxSmem = 200 * 1024;
+    const size_t smem = (size_t)(2 * max_ny + 4 * max_P) * sizeof(float);
+    if (smem <= kMaxSmem) {
+        static bool configured[64] = {};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev < 0 || dev >= 64 || !configured[dev]) {
+            cudaFuncSetAttribute(k_twin_batch_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kMaxSmem);
+            if (dev >= 0 && dev < 64) configured[dev] = true;
+        }
+        k_twin_batch_smem<<<n, 512, smem, st>>>(tws, step_base, steps);
+    } else {
+        k_twin_batch_global<<<n, 1024, 0, st>>>(tws, step_base, steps);
+    }
 }
 
 // Flux sums (Sec. 2.6, Poynting form): out[0] = sum_i Re(E_r conj(H_r)),

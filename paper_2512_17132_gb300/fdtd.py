@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "libfdtd.so")
 FDTD_OK, FDTD_EINVAL, FDTD_ENOMEM, FDTD_ECUDA = 0, -1, -2, -3
 FDTD_EUNSTABLE, FDTD_ETIMEOUT, FDTD_ESTATE = -4, -5, -6
 FDTD_OPT_KERNEL, FDTD_OPT_BLOCK_STEPS, FDTD_OPT_SEG_ROWS = 1, 2, 3
-FDTD_OPT_TIMING, FDTD_OPT_WATCHDOG, FDTD_OPT_VARIANT = 4, 5, 6
+FDTD_OPT_TIMING, FDTD_OPT_WATCHDOG, FDTD_OPT_VARIANT, FDTD_OPT_GRAPH = 4, 5, 6, 7
 KERNEL_AUTO, KERNEL_NAIVE, KERNEL_BLOCKED = 0, 1, 2
 
 
@@ -79,6 +79,14 @@ def load_library(path: str = LIB_PATH):
         "fdtd_get_stats": (C.c_int, [vp, C.POINTER(fdtd_stats)]),
         "fdtd_last_error": (C.c_char_p, [vp]),
         "fdtd_destroy": (None, [vp]),
+        "fdtd_autotune": (C.c_int, [vp, i32]),
+        "fdtd_batch_create": (C.c_int, [C.POINTER(vp), i32, C.POINTER(vp)]),
+        "fdtd_batch_set_option": (C.c_int, [vp, i32, i64]),
+        "fdtd_batch_autotune": (C.c_int, [vp, i32]),
+        "fdtd_batch_run": (C.c_int, [vp, i64]),
+        "fdtd_batch_get_stats": (C.c_int, [vp, C.POINTER(fdtd_stats)]),
+        "fdtd_batch_last_error": (C.c_char_p, [vp]),
+        "fdtd_batch_destroy": (None, [vp]),
         "fdtd_blocked_advance_noalloc": (C.c_int, [C.POINTER(fdtd_grid), vp,
                                                    C.POINTER(fdtd_material), i32, C.c_double,
                                                    C.POINTER(vp), C.POINTER(vp), i32, vp,
@@ -219,6 +227,94 @@ def fdtd_last_error(h=None) -> str:
 def fdtd_destroy(h):
     if h:
         load_library().fdtd_destroy(h)
+
+
+def fdtd_autotune(h, trial_launches: int = 4):
+    _check(load_library().fdtd_autotune(h, int(trial_launches)), h)
+
+
+def _check_batch(code, b):
+    if code != FDTD_OK:
+        msg = load_library().fdtd_batch_last_error(b)
+        raise FDTDError(code, msg.decode() if msg else "")
+
+
+def fdtd_batch_create(handles):
+    arr = (C.c_void_p * len(handles))(*[h.value if isinstance(h, C.c_void_p) else h
+                                         for h in handles])
+    out = C.c_void_p()
+    _check_batch(load_library().fdtd_batch_create(arr, len(handles), C.byref(out)), None)
+    return out
+
+
+def fdtd_batch_set_option(b, option: int, value: int):
+    _check_batch(load_library().fdtd_batch_set_option(b, int(option), int(value)), b)
+
+
+def fdtd_batch_autotune(b, trial_launches: int = 4):
+    _check_batch(load_library().fdtd_batch_autotune(b, int(trial_launches)), b)
+
+
+def fdtd_batch_run(b, steps: int):
+    _check_batch(load_library().fdtd_batch_run(b, int(steps)), b)
+
+
+def fdtd_batch_get_stats(b) -> dict:
+    st = fdtd_stats()
+    _check_batch(load_library().fdtd_batch_get_stats(b, C.byref(st)), b)
+    d = {k: getattr(st, k) for k, _ in fdtd_stats._fields_ if k != "reserved"}
+    d["graph"] = bool(st.reserved)
+    return d
+
+
+def fdtd_batch_last_error(b=None) -> str:
+    m = load_library().fdtd_batch_last_error(b)
+    return m.decode() if m else ""
+
+
+def fdtd_batch_destroy(b):
+    if b:
+        load_library().fdtd_batch_destroy(b)
+
+
+class Batch:
+    """Owner of one fdtd_batch over a list of Simulation objects."""
+
+    def __init__(self, sims, timing=False, graph=True):
+        self.sims = list(sims)
+        self.b = fdtd_batch_create([s.h for s in self.sims])
+        if timing:
+            fdtd_batch_set_option(self.b, FDTD_OPT_TIMING, 1)
+        if not graph:
+            fdtd_batch_set_option(self.b, FDTD_OPT_GRAPH, 0)
+
+    def autotune(self, trial_launches=4):
+        fdtd_batch_autotune(self.b, trial_launches)
+        return self
+
+    def run(self, steps):
+        fdtd_batch_run(self.b, steps)
+        return self
+
+    def stats(self):
+        return fdtd_batch_get_stats(self.b)
+
+    def close(self):
+        if self.b:
+            fdtd_batch_destroy(self.b)
+            self.b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def fdtd_blocked_advance_noalloc(grid: fdtd_grid, labels, materials, lambda0: float,
