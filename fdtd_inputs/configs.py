@@ -223,12 +223,13 @@ def config_c3(lambda0: float = 550e-9, diseased: bool = False, seed: int = 0,
 
 
 def config_c4(n_sims: int = 64, seed: int = 0, steps: int = 30000,
-              nx: int = 2000, height_range=(2000, 12500)) -> list:
+              nx: int = 2000, height_range=(2000, 12500), coarse: int = 4) -> list:
     """Config 4: independent dicot simulations of uneven height.
 
     Heights are uniform in height_range (rounded to 4 rows), wavelengths lie on
     a 400-2500 nm grid shuffled by the seed, even indices are healthy and odd
-    indices carry hyphae.
+    indices carry hyphae. Label maps are drawn `coarse` times coarser and
+    repeated (the layer edges are rounded to multiples of `coarse`).
     """
     from .geometry import dicot_labels
     rng = np.random.default_rng(seed)
@@ -240,8 +241,9 @@ def config_c4(n_sims: int = 64, seed: int = 0, steps: int = 30000,
     for i in range(n_sims):
         ny = int(heights[i])
         rows = dicot_rows(ny, dx)
+        rows["layer_edges"] = [e // coarse * coarse for e in rows["layer_edges"]]
         labels = dicot_labels(nx, ny, dx, rows, seed=1000 + i,
-                              n_hyphae=(3 if i % 2 else 0))
+                              n_hyphae=(3 if i % 2 else 0), coarse=coarse)
         specs.append(_base(f"c4-{i}", nx, ny, dx, steps, float(lams[i]), rows,
                            labels, leaf_materials(float(lams[i]))))
     return specs

@@ -209,11 +209,18 @@ def _add_hyphae(rng, lab, top_row, per_um, n):
 
 
 def dicot_labels(nx: int, ny: int, dx: float, rows: dict, seed: int = 0,
-                 n_hyphae: int = 0) -> np.ndarray:
+                 n_hyphae: int = 0, coarse: int = 1) -> np.ndarray:
     """Dicot-like cross-section: cuticle, an upper epidermis of 15 x 12 um
     ellipse cells, palisade columns of 10 x 40 um ellipses, spongy mesophyll of
     Voronoi cells shrunk to a 40 % air fraction, a lower epidermis, with
-    0.3 um walls, 1 um cytoplasm linings and chloroplasts in the mesophyll."""
+    0.3 um walls, 1 um cytoplasm linings and chloroplasts in the mesophyll.
+    coarse > 1 draws the map on a grid `coarse` times coarser and repeats each
+    cell (faster for large batches; nx, ny and the layer edges must divide)."""
+    if coarse > 1:
+        rc = dict(rows, layer_edges=[e // coarse for e in rows["layer_edges"]])
+        small = dicot_labels(nx // coarse, ny // coarse, dx * coarse, rc, seed=seed,
+                             n_hyphae=n_hyphae)
+        return np.ascontiguousarray(np.repeat(np.repeat(small, coarse, 0), coarse, 1))
     rng = np.random.default_rng(seed)
     per_um = 1e-6 / dx
     e = rows["layer_edges"]

@@ -180,6 +180,7 @@ class TMzOracle:
         self.n = 0
         self.dft = {k: np.zeros(self.nx, dtype=np.complex128)
                     for k in ("e_r", "h_r", "e_t", "h_t")}
+        self.tape = None          # list: (Ez^{n-1/2}, curl^n) per step when recording
 
     # -- CPML ---------------------------------------------------------------
     def _setup_cpml(self, spec):
@@ -223,6 +224,8 @@ class TMzOracle:
             psi *= b
             psi += c * d_hx[rows] / dx
             curl[rows] = d_hy[rows] / dx + d_hx[rows] / (k * dx) + psi
+        if self.tape is not None:
+            self.tape.append((self.ez, curl))
         self.ez = self.ce * self.ez + self.ce_curl * curl
 
         tE = (self.n + 0.5) * self.dt
