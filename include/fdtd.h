@@ -132,6 +132,13 @@ int fdtd_create(const fdtd_grid* grid, const uint8_t* labels,
                 const fdtd_source* source, void* cuda_stream,
                 fdtd_handle** out);
 
+/* As fdtd_create, with per-cell materials instead of labels: eps_r and sigma
+ * (ny*nx doubles each, [S/m] for sigma, host or device, copied) at the run's
+ * wavelength. Rows tfsf_row-1 and tfsf_row must be air (eps_r = 1,
+ * sigma = 0). Such handles step with the per-half-step kernels. */
+int fdtd_create_maps(const fdtd_grid* grid, const double* eps_r, const double* sigma,
+                     const fdtd_source* source, void* cuda_stream, fdtd_handle** out);
+
 /* Advance by `steps` (>= 0) leapfrog steps (Sec. 2.3), accumulating the
  * monitor DFTs, and the empty-domain reference run by the same steps.
  * Asynchronous on the handle's stream; host work (the incident-wave tables)
@@ -188,6 +195,24 @@ const char* fdtd_last_error(const fdtd_handle* h);
 /* Release the handle and its device memory (waits for its work). NULL is a
  * no-op. */
 void fdtd_destroy(fdtd_handle* h);
+
+/* Discrete adjoint (reverse-mode gradient of the leapfrog recursion) of
+ * J = wR R + wT T (R, T as in fdtd_flux).
+ * fdtd_forward_checkpointed: reset, run `steps` steps and keep the full state
+ * every `every` steps on the device (about 12 bytes per cell each).
+ * fdtd_backward: for J at the end of that run, dJ/d(eps_r) and dJ/d(sigma)
+ * per cell (ny*nx doubles each, host or device, NULL to skip) and, for
+ * labelled handles, dJ/dn and dJ/dk per label (n_labels pairs, host or
+ * device, NULL to skip); out = {J, R, T} (may be NULL). Segment by segment
+ * (last first) the states are recomputed from their checkpoint into a device
+ * tape of `every` states (about 12*every bytes per cell, freed on return)
+ * and the transpose of every update is applied in reverse order; per-segment
+ * FP32 sums are accumulated in FP64. The handle keeps its final forward
+ * state. FDTD_ESTATE if no checkpointed run precedes or no incident power
+ * reached t_row. Synchronises. */
+int fdtd_forward_checkpointed(fdtd_handle* h, int64_t steps, int32_t every);
+int fdtd_backward(fdtd_handle* h, double wR, double wT, double* g_eps, double* g_sigma,
+                  double* g_label, double out[3]);
 
 /* Pick the blocked kernel's steps per launch, code shape and segment height
  * for this handle's grid by timing `trial_launches` launches of each

@@ -1,0 +1,503 @@
+// Discrete adjoint of R and T: gradients with respect to the per-cell
+// (eps_r, sigma) and the per-label (n, kappa).
+//
+// fdtd_forward_checkpointed runs the forward loop from step 0 and stores the
+// full state every C steps on the device. fdtd_backward then walks the
+// segments last to first: it recomputes the segment's states from its
+// checkpoint into a device tape (the forward arithmetic exactly, so the tape
+// holds the states the forward run produced) and applies, step by step in
+// reverse, the transpose of every update of the leapfrog step:
+//
+//   forward step n                         reverse step n
+//   Ez <- ca Ez + cb curl(H, psi_E)        H monitor sources; transpose of the
+//   Hx, Hy <- H + S dEz (+ psi_H)          H updates (psi_H carry); E monitor
+//   DFTs of Ez and averaged Hx             source; gca += lE Ez^{n-1/2},
+//                                          gcb += lE curl^n; transpose of the
+//                                          E update (psi_E carry), lE <- ca lE
+//
+// in the library's units (Ez, eta0 H; ca, cb of Sec. 2.3). The monitor
+// sources follow from J = wR R + wT T with R, T the Poynting ratios of
+// Sec. 2.6 and the final DFT sums; the incident power does not depend on the
+// cells. Per-segment FP32 gradient sums are added into FP64 totals, which
+// are finally chained through ca(eps_r, sigma), cb(eps_r, sigma) and, for
+// labelled handles, through eps_r = n^2 - k^2, sigma = 2 w0 eps0 n k
+// (Sec. 2.2) with a per-label reduction.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "fdtd_internal.h"
+
+using namespace fdtd;
+
+namespace {
+
+constexpr double kC0 = 299792458.0;
+constexpr double kPi = 3.14159265358979323846;
+
+#define ACK(call)                                                                   \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess) {                                                    \
+            h->err = std::string(#call) + ": " + cudaGetErrorString(e_);            \
+            throw Fail{e_ == cudaErrorMemoryAllocation ? FDTD_ENOMEM : FDTD_ECUDA}; \
+        }                                                                           \
+    } while (0)
+
+struct AdjArgs {
+    int nx, ny, pitch, lpitch, P, js, jr, jt;
+    float S;
+    const uint8_t* labels;
+    const float2* coef;
+    const float2* cellcoef;
+    const float* pml_e;
+    const float* pml_h;
+    const float* hinc;
+    const double2* phE;
+    const double2* phH;
+    const double2* dft;     // final DFT sums [4][nx]
+    double kR, kT;          // dJ/d Re(E conj H) per monitor row
+    float* lE; float* lX; float* lY;
+    float* mE; float* mH;   // CPML carries [2P][pitch]
+    float* D; float* C; float* DX;
+    float* gA; float* gB;   // FP32 per-segment sums
+    const float* tE; const float* tX; const float* tY; const float* tPE;   // tape state of step n
+};
+
+__device__ __forceinline__ float2 cell_coef(const AdjArgs& a, int j, int i) {
+    const size_t o = (size_t)j * a.pitch + i;
+    return a.cellcoef ? a.cellcoef[o] : a.coef[a.labels[(size_t)j * a.lpitch + i]];
+}
+
+// monitor source of Hx^{n+1} at row j (rows jr, jr+1, jt, jt+1)
+__device__ __forceinline__ float src_h(const AdjArgs& a, int j, int i, int64_t n) {
+    double s = 0.0;
+    const double2 ph = a.phH[n];
+    if (j == a.jr || j == a.jr + 1) {
+        const double2 e = a.dft[i];
+        s += 0.5 * a.kR * (e.x * ph.x + e.y * ph.y);
+    }
+    if (j == a.jt || j == a.jt + 1) {
+        const double2 e = a.dft[2 * a.nx + i];
+        s += 0.5 * a.kT * (e.x * ph.x + e.y * ph.y);
+    }
+    return (float)s;
+}
+
+__device__ __forceinline__ float src_e(const AdjArgs& a, int j, int i, int64_t n) {
+    double s = 0.0;
+    const double2 pe = a.phE[n];
+    if (j == a.jr) {
+        const double2 hh = a.dft[a.nx + i];
+        s += a.kR * (hh.x * pe.x + hh.y * pe.y);
+    }
+    if (j == a.jt) {
+        const double2 hh = a.dft[3 * a.nx + i];
+        s += a.kT * (hh.x * pe.x + hh.y * pe.y);
+    }
+    return (float)s;
+}
+
+// transpose of the Hx update (with the psi_H carry) and the H monitor source
+__global__ void k_adj_h1(AdjArgs a, int64_t n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= a.nx) return;
+    const size_t o = (size_t)j * a.pitch + i;
+    float x = a.lX[o];
+    if (j == a.jr || j == a.jr + 1 || j == a.jt || j == a.jt + 1) {
+        x = __fadd_rn(x, src_h(a, j, i, n));
+        a.lX[o] = x;
+    }
+    float d = 0.f;
+    if (j > 0) {
+        const int ph = pml_h_index(j, a.ny, a.P);
+        if (ph >= 0) {
+            float* m = a.mH + (size_t)ph * a.pitch + i;
+            const float sx = __fmul_rn(a.S, x);
+            const float nu = __fadd_rn(sx, *m);
+            d = __fmaf_rn(a.pml_h[2 * a.P + ph], nu, __fmul_rn(sx, a.pml_h[4 * a.P + ph]));
+            *m = __fmul_rn(a.pml_h[ph], nu);
+        } else {
+            d = __fmul_rn(a.S, x);
+        }
+    }
+    a.D[o] = d;
+}
+
+// adjoint of Ez^{n+1/2}: carried part + Hy and Hx transposes + E monitor source
+__global__ void k_adj_h2(AdjArgs a, int64_t n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= a.nx) return;
+    const size_t o = (size_t)j * a.pitch + i;
+    const int ir = (i + 1 == a.nx) ? 0 : i + 1;
+    float e = a.lE[o];
+    e = __fadd_rn(e, __fmul_rn(a.S, __fsub_rn(a.lY[o], a.lY[(size_t)j * a.pitch + ir])));
+    const float dn = (j + 1 < a.ny) ? a.D[o + a.pitch] : 0.f;
+    e = __fadd_rn(e, __fsub_rn(a.D[o], dn));
+    if (j == a.jr || j == a.jt) e = __fadd_rn(e, src_e(a, j, i, n));
+    a.lE[o] = e;
+}
+
+// gradient sums and the transpose of the Ez update (with the psi_E carry)
+__global__ void k_adj_e1(AdjArgs a, int64_t n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= a.nx) return;
+    const size_t o = (size_t)j * a.pitch + i;
+    const int ir = (i + 1 == a.nx) ? 0 : i + 1;
+    const float eb = a.lE[o];
+    // forward curl of step n from the taped state (same rounding as forward)
+    const float dhy = __fsub_rn(a.tY[(size_t)j * a.pitch + ir], a.tY[o]);
+    const float hxb = (j + 1 < a.ny) ? a.tX[o + a.pitch] : 0.0f;
+    float dhx = __fsub_rn(hxb, a.tX[o]);
+    if (j == a.js) dhx = __fsub_rn(dhx, a.hinc[n]);
+    const int pe = pml_e_index(j, a.ny, a.P);
+    float curl;
+    const float2 c = cell_coef(a, j, i);
+    const float cbar = __fmul_rn(c.y, eb);
+    float gx;
+    if (pe >= 0) {
+        const float b = a.pml_e[pe], cc = a.pml_e[2 * a.P + pe], ik = a.pml_e[4 * a.P + pe];
+        const float psi = psi_new(b, cc, a.tPE[(size_t)pe * a.pitch + i], dhx);
+        curl = __fadd_rn(dhy, __fmaf_rn(dhx, ik, psi));
+        float* m = a.mE + (size_t)pe * a.pitch + i;
+        const float rho = __fadd_rn(cbar, *m);
+        gx = __fmaf_rn(cc, rho, __fmul_rn(cbar, ik));
+        *m = __fmul_rn(b, rho);
+    } else {
+        curl = __fadd_rn(dhy, dhx);
+        gx = cbar;
+    }
+    a.gA[o] = __fmaf_rn(eb, a.tE[o], a.gA[o]);
+    a.gB[o] = __fmaf_rn(eb, curl, a.gB[o]);
+    a.C[o] = cbar;
+    a.DX[o] = gx;
+    a.lE[o] = __fmul_rn(c.x, eb);
+}
+
+// transposes of d_hy = Hy[i+1] - Hy[i] and d_hx = Hx[j+1] - Hx[j]
+__global__ void k_adj_e2(AdjArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= a.nx) return;
+    const size_t o = (size_t)j * a.pitch + i;
+    const int il = (i == 0) ? a.nx - 1 : i - 1;
+    a.lY[o] = __fadd_rn(a.lY[o], __fsub_rn(a.C[(size_t)j * a.pitch + il], a.C[o]));
+    const float up = (j > 0) ? a.DX[o - a.pitch] : 0.f;
+    a.lX[o] = __fadd_rn(a.lX[o], __fsub_rn(up, a.DX[o]));
+}
+
+__global__ void k_adj_flush(float* gA, float* gB, double* GA, double* GB, int nx, int ny,
+                            int pitch) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= nx) return;
+    const size_t o = (size_t)j * pitch + i;
+    GA[o] += (double)gA[o];
+    GB[o] += (double)gB[o];
+    gA[o] = 0.f;
+    gB[o] = 0.f;
+}
+
+struct ChainArgs {
+    int nx, ny, pitch, lpitch, n_labels;
+    double S, dt, eps0, w;
+    const uint8_t* labels;
+    const double* mat;        // [n_labels][2] (n, k) for labelled handles
+    const double* cell_eps;   // per-cell maps or null
+    const double* cell_sig;
+    const double* GA; const double* GB;
+    double* g_eps; double* g_sig;   // dense ny*nx (device)
+    double* g_lab;                  // [n_labels][2] or null
+};
+
+// dJ/d(eps_r), dJ/d(sigma) per cell and the per-label (n, kappa) sums
+__global__ void k_adj_chain(ChainArgs a) {
+    __shared__ double s_lab[256 * 2];
+    for (int t = threadIdx.x; t < 512; t += blockDim.x) s_lab[t] = 0.0;
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i < a.nx) {
+        const size_t o = (size_t)j * a.pitch + i;
+        double eps, sig, n = 0, k = 0;
+        int l = 0;
+        if (a.cell_eps) {
+            eps = a.cell_eps[(size_t)j * a.nx + i];
+            sig = a.cell_sig[(size_t)j * a.nx + i];
+        } else {
+            l = a.labels[(size_t)j * a.lpitch + i];
+            n = a.mat[2 * l];
+            k = a.mat[2 * l + 1];
+            eps = n * n - k * k;
+            sig = 2.0 * a.w * a.eps0 * n * k;
+        }
+        const double b = sig * a.dt / (2.0 * a.eps0 * eps);
+        const double q = (1.0 + b) * (1.0 + b);
+        const double dca_de = 2.0 * b / (eps * q);
+        const double dca_ds = -a.dt / (a.eps0 * eps * q);
+        const double dcb_de = -a.S / (eps * eps * q);
+        const double dcb_ds = -a.S * a.dt / (2.0 * a.eps0 * eps * eps * q);
+        const double ge = a.GA[o] * dca_de + a.GB[o] * dcb_de;
+        const double gs = a.GA[o] * dca_ds + a.GB[o] * dcb_ds;
+        a.g_eps[(size_t)j * a.nx + i] = ge;
+        a.g_sig[(size_t)j * a.nx + i] = gs;
+        if (a.g_lab) {
+            atomicAdd(&s_lab[2 * l], ge * 2.0 * n + gs * 2.0 * a.w * a.eps0 * k);
+            atomicAdd(&s_lab[2 * l + 1], -ge * 2.0 * k + gs * 2.0 * a.w * a.eps0 * n);
+        }
+    }
+    __syncthreads();
+    if (a.g_lab)
+        for (int t = threadIdx.x; t < 2 * a.n_labels; t += blockDim.x)
+            if (s_lab[t] != 0.0) atomicAdd(&a.g_lab[t], s_lab[t]);
+}
+
+size_t state_floats(const fdtd_handle* h) {
+    return (size_t)3 * h->pitch * h->g.ny + (size_t)2 * std::max(2 * h->g.pml_cells, 1) * h->pitch;
+}
+
+// views of one packed state: Ez, Hx, Hy, psi_E, psi_H
+struct StateView {
+    float *E, *X, *Y, *PE, *PH;
+};
+StateView view(const fdtd_handle* h, float* base) {
+    const size_t f = (size_t)h->pitch * h->g.ny;
+    const size_t p = (size_t)std::max(2 * h->g.pml_cells, 1) * h->pitch;
+    return {base, base + f, base + 2 * f, base + 3 * f, base + 3 * f + p};
+}
+
+void copy_state_out(fdtd_handle* h, float* dst) {
+    const size_t f = (size_t)h->pitch * h->g.ny * sizeof(float);
+    const size_t p = (size_t)std::max(2 * h->g.pml_cells, 1) * h->pitch * sizeof(float);
+    const StateView v = view(h, dst);
+    const int c = h->cur;
+    ACK(cudaMemcpyAsync(v.E, h->ez[c], f, cudaMemcpyDeviceToDevice, h->stream));
+    ACK(cudaMemcpyAsync(v.X, h->hx[c], f, cudaMemcpyDeviceToDevice, h->stream));
+    ACK(cudaMemcpyAsync(v.Y, h->hy[c], f, cudaMemcpyDeviceToDevice, h->stream));
+    ACK(cudaMemcpyAsync(v.PE, h->psiE[c], p, cudaMemcpyDeviceToDevice, h->stream));
+    ACK(cudaMemcpyAsync(v.PH, h->psiH[c], p, cudaMemcpyDeviceToDevice, h->stream));
+}
+
+// One forward step n from state `in` to state `out` (no monitor sums).
+void step_out_of_place(fdtd_handle* h, const StateView& in, const StateView& out, int64_t n,
+                       double2* dummy) {
+    StepArgs s = step_args(h);
+    s.dft = dummy;
+    const size_t f = (size_t)h->pitch * h->g.ny * sizeof(float);
+    const size_t p = (size_t)std::max(2 * h->g.pml_cells, 1) * h->pitch * sizeof(float);
+    if (!h->maps && h->g.nx % 4 == 0) {
+        BlockPlan* pl = nullptr;
+        for (auto& q : h->plans)
+            if (q.K == 1 && q.d_seg_y0) pl = &q;
+        if (pl) {
+            BlockedArgs b{};
+            b.s = s;
+            b.ez_in = in.E; b.hx_in = in.X; b.hy_in = in.Y;
+            b.ez_out = out.E; b.hx_out = out.X; b.hy_out = out.Y;
+            b.psiE_in = in.PE; b.psiH_in = in.PH; b.psiE_out = out.PE; b.psiH_out = out.PH;
+            b.slotE = h->slotE; b.slotH = h->slotH;
+            b.seg_y0 = pl->d_seg_y0;
+            b.n_strips = pl->n_strips;
+            b.n_tasks = pl->n_strips * pl->n_segs;
+            b.w_int = pl->w_int;
+            launch_blocked(b, 1, 0, n, h->stream);
+            return;
+        }
+    }
+    ACK(cudaMemcpyAsync(out.E, in.E, f, cudaMemcpyDeviceToDevice, h->stream));
+    ACK(cudaMemcpyAsync(out.X, in.X, f, cudaMemcpyDeviceToDevice, h->stream));
+    ACK(cudaMemcpyAsync(out.Y, in.Y, f, cudaMemcpyDeviceToDevice, h->stream));
+    ACK(cudaMemcpyAsync(out.PE, in.PE, p, cudaMemcpyDeviceToDevice, h->stream));
+    ACK(cudaMemcpyAsync(out.PH, in.PH, p, cudaMemcpyDeviceToDevice, h->stream));
+    launch_naive_step(s, out.E, out.X, out.Y, out.PE, out.PH, n, h->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+int fdtd_forward_checkpointed(fdtd_handle* h, int64_t steps, int32_t every) {
+    if (!h) return FDTD_EINVAL;
+    try {
+        if (steps < 1 || every < 1) {
+            h->err = "fdtd_forward_checkpointed: need steps >= 1 and every >= 1";
+            return FDTD_EINVAL;
+        }
+        ACK(cudaSetDevice(h->device));
+        const int rc = fdtd_reset(h);
+        if (rc != FDTD_OK) return rc;
+        const int64_t n_ck = (steps + every - 1) / every;
+        const size_t sf = state_floats(h);
+        if ((int64_t)h->ck.size() != n_ck || h->ck_floats != sf) {
+            ACK(cudaStreamSynchronize(h->stream));
+            for (auto& c : h->ck) { cudaFree(c); c = nullptr; }
+            h->ck.assign((size_t)n_ck, nullptr);
+            for (auto& c : h->ck) ACK(cudaMalloc(&c, sf * sizeof(float)));
+            h->ck_floats = sf;
+        }
+        h->adj_valid = false;
+        for (int64_t c = 0; c < n_ck; ++c) {
+            copy_state_out(h, h->ck[(size_t)c]);
+            const int r = fdtd_run(h, std::min<int64_t>(every, steps - c * every));
+            if (r != FDTD_OK) return r;
+        }
+        h->adj_steps = steps;
+        h->adj_every = every;
+        h->adj_valid = true;
+        return FDTD_OK;
+    } catch (const Fail& f) {
+        return f.code;
+    }
+}
+
+int fdtd_backward(fdtd_handle* h, double wR, double wT, double* g_eps, double* g_sigma,
+                  double* g_label, double out[3]) {
+    if (!h) return FDTD_EINVAL;
+    std::vector<float*> tape;
+    float* buf = nullptr;
+    double* dbl = nullptr;
+    double2* dummy = nullptr;
+    auto cleanup = [&]() {
+        for (auto& t : tape) cudaFree(t);
+        if (buf) cudaFree(buf);
+        if (dbl) cudaFree(dbl);
+        if (dummy) cudaFree(dummy);
+    };
+    try {
+        if (!h->adj_valid || h->n != h->adj_steps) {
+            h->err = "fdtd_backward: run fdtd_forward_checkpointed first (and no steps since)";
+            return FDTD_ESTATE;
+        }
+        ACK(cudaSetDevice(h->device));
+        double flux[3];
+        int rc = fdtd_flux_raw(h, flux);
+        if (rc != FDTD_OK) return rc;
+        double R = 0, T = 0;
+        rc = fdtd_flux(h, &R, &T);
+        if (rc != FDTD_OK) return rc;
+        const double s0 = h->h_flux[2];
+        if (!(s0 != 0.0)) {
+            h->err = "fdtd_backward: no incident power at t_row (run longer)";
+            return FDTD_ESTATE;
+        }
+        const fdtd_grid& g = h->g;
+        const int nx = g.nx, ny = g.ny, pitch = h->pitch;
+        const size_t f = (size_t)pitch * ny;
+        const size_t pr = (size_t)std::max(2 * g.pml_cells, 1) * pitch;
+        const int every = h->adj_every;
+        const int64_t steps = h->adj_steps;
+        if (!h->maps && nx % 4 == 0) {
+            // segment plan and scratch of the one-step blocked kernel used to recompute
+            const int keep = h->opt_seg;
+            h->opt_seg = 0;
+            get_plan(h, 1);
+            h->opt_seg = keep;
+        }
+        const size_t sf = state_floats(h);
+        tape.assign((size_t)std::min<int64_t>(every, steps), nullptr);
+        for (auto& t : tape) ACK(cudaMalloc(&t, sf * sizeof(float)));
+        // lE lX lY D C DX gA gB (f each) + mE mH (pr each)
+        ACK(cudaMalloc(&buf, (8 * f + 2 * pr) * sizeof(float)));
+        ACK(cudaMemsetAsync(buf, 0, (8 * f + 2 * pr) * sizeof(float), h->stream));
+        ACK(cudaMalloc(&dbl, 2 * f * sizeof(double)));
+        ACK(cudaMemsetAsync(dbl, 0, 2 * f * sizeof(double), h->stream));
+        ACK(cudaMalloc(&dummy, (size_t)4 * nx * sizeof(double2)));
+        AdjArgs a{};
+        a.nx = nx; a.ny = ny; a.pitch = pitch; a.lpitch = h->lpitch; a.P = g.pml_cells;
+        a.js = g.tfsf_row; a.jr = g.r_row; a.jt = g.t_row; a.S = (float)h->S;
+        a.labels = h->labels; a.coef = h->coef; a.cellcoef = h->cellcoef;
+        a.pml_e = h->pml_e; a.pml_h = h->pml_h; a.hinc = h->d_hinc;
+        a.phE = h->d_phE; a.phH = h->d_phH; a.dft = h->dft;
+        a.kR = wR / (-(double)nx * s0);
+        a.kT = wT / ((double)nx * s0);
+        a.lE = buf; a.lX = buf + f; a.lY = buf + 2 * f; a.D = buf + 3 * f; a.C = buf + 4 * f;
+        a.DX = buf + 5 * f; a.gA = buf + 6 * f; a.gB = buf + 7 * f;
+        a.mE = buf + 8 * f; a.mH = buf + 8 * f + pr;
+        double* GA = dbl;
+        double* GB = dbl + f;
+        const dim3 blk(256), grd((nx + 255) / 256, ny);
+        const int64_t n_seg = (steps + every - 1) / every;
+        for (int64_t c = n_seg - 1; c >= 0; --c) {
+            const int64_t c0 = c * every;
+            const int L = (int)std::min<int64_t>(every, steps - c0);
+            ACK(cudaMemcpyAsync(tape[0], h->ck[(size_t)c], sf * sizeof(float),
+                                cudaMemcpyDeviceToDevice, h->stream));
+            for (int m = 0; m + 1 < L; ++m)
+                step_out_of_place(h, view(h, tape[m]), view(h, tape[m + 1]), c0 + m, dummy);
+            for (int m = L - 1; m >= 0; --m) {
+                const int64_t n = c0 + m;
+                const StateView v = view(h, tape[m]);
+                a.tE = v.E; a.tX = v.X; a.tY = v.Y; a.tPE = v.PE;
+                k_adj_h1<<<grd, blk, 0, h->stream>>>(a, n);
+                k_adj_h2<<<grd, blk, 0, h->stream>>>(a, n);
+                k_adj_e1<<<grd, blk, 0, h->stream>>>(a, n);
+                k_adj_e2<<<grd, blk, 0, h->stream>>>(a);
+            }
+            k_adj_flush<<<grd, blk, 0, h->stream>>>(a.gA, a.gB, GA, GB, nx, ny, pitch);
+            h->total_launches += 4 * L + 1;
+            ACK(cudaGetLastError());
+        }
+        // chain rule to (eps_r, sigma) per cell and (n, kappa) per label
+        double* d_ge = nullptr;
+        double* d_gs = nullptr;
+        double* d_gl = nullptr;
+        double* d_mat = nullptr;
+        const size_t cells = (size_t)nx * ny;
+        ACK(cudaMalloc(&d_ge, cells * sizeof(double)));
+        ACK(cudaMalloc(&d_gs, cells * sizeof(double)));
+        ChainArgs ch{};
+        ch.nx = nx; ch.ny = ny; ch.pitch = pitch; ch.lpitch = h->lpitch; ch.n_labels = h->n_labels;
+        ch.S = h->S; ch.dt = g.dt;
+        ch.eps0 = 1.0 / (4.0e-7 * kPi * kC0 * kC0);
+        ch.w = 2.0 * kPi * kC0 / h->src.lambda0;
+        ch.labels = h->labels;
+        ch.GA = GA; ch.GB = GB; ch.g_eps = d_ge; ch.g_sig = d_gs;
+        if (h->maps) {
+            ch.cell_eps = h->cell_eps;
+            ch.cell_sig = h->cell_sig;
+        } else {
+            std::vector<double> mat(2 * h->n_labels);
+            for (int l = 0; l < h->n_labels; ++l) {
+                mat[2 * l] = h->table[l].n;
+                mat[2 * l + 1] = h->table[l].k;
+            }
+            ACK(cudaMalloc(&d_mat, mat.size() * sizeof(double)));
+            ACK(cudaMemcpy(d_mat, mat.data(), mat.size() * sizeof(double), cudaMemcpyHostToDevice));
+            ACK(cudaMalloc(&d_gl, mat.size() * sizeof(double)));
+            ACK(cudaMemsetAsync(d_gl, 0, mat.size() * sizeof(double), h->stream));
+            ch.mat = d_mat;
+            ch.g_lab = d_gl;
+        }
+        k_adj_chain<<<grd, blk, 0, h->stream>>>(ch);
+        h->total_launches += 1;
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e == cudaSuccess && g_eps)
+            e = cudaMemcpy(g_eps, d_ge, cells * sizeof(double), cudaMemcpyDefault);
+        if (e == cudaSuccess && g_sigma)
+            e = cudaMemcpy(g_sigma, d_gs, cells * sizeof(double), cudaMemcpyDefault);
+        if (e == cudaSuccess && g_label && d_gl)
+            e = cudaMemcpy(g_label, d_gl, 2 * h->n_labels * sizeof(double), cudaMemcpyDefault);
+        cudaFree(d_ge); cudaFree(d_gs);
+        if (d_gl) cudaFree(d_gl);
+        if (d_mat) cudaFree(d_mat);
+        ACK(e);
+        if (out) {
+            out[0] = wR * R + wT * T;
+            out[1] = R;
+            out[2] = T;
+        }
+        cleanup();
+        return FDTD_OK;
+    } catch (const Fail& fl) {
+        cleanup();
+        return fl.code;
+    }
+}
+
+}  // extern "C"

@@ -76,7 +76,8 @@ StepArgs step_args(fdtd_handle* h) {
     a.nx = h->g.nx; a.ny = h->g.ny; a.pitch = h->pitch; a.lpitch = h->lpitch;
     a.P = h->g.pml_cells; a.js = h->g.tfsf_row; a.jr = h->g.r_row; a.jt = h->g.t_row;
     a.n_labels = h->n_labels; a.S = (float)h->S;
-    a.labels = h->labels; a.coef = h->coef; a.pml_e = h->pml_e; a.pml_h = h->pml_h;
+    a.labels = h->labels; a.coef = h->coef; a.cellcoef = h->cellcoef;
+    a.pml_e = h->pml_e; a.pml_h = h->pml_h;
     a.hinc = h->d_hinc; a.einc = h->d_einc; a.phE = h->d_phE; a.phH = h->d_phH;
     a.dft = h->dft;
     return a;
@@ -222,7 +223,7 @@ BlockPlan& get_plan(fdtd_handle* h, int K) {
 }
 
 int choose_kernel(fdtd_handle* h) {
-    if (h->opt_kernel == 1) return 1;
+    if (h->opt_kernel == 1 || h->maps) return 1;   // per-cell materials: per-half-step kernels
     const bool blocked_ok = (h->g.nx % 4 == 0);
     if (h->opt_kernel == 2 && !blocked_ok) {
         h->err = "the blocked kernel needs nx % 4 == 0";
@@ -322,6 +323,9 @@ void free_all(fdtd_handle* h) {
         dfree(h->psiE[i]); dfree(h->psiH[i]);
     }
     dfree(h->labels); dfree(h->coef); dfree(h->pml_e); dfree(h->pml_h); dfree(h->dft);
+    dfree(h->cellcoef); dfree(h->cell_eps); dfree(h->cell_sig);
+    for (auto& c : h->ck) dfree(c);
+    h->ck.clear();
     dfree(h->tw_ez); dfree(h->tw_hx); dfree(h->tw_psiE); dfree(h->tw_psiH); dfree(h->tw_dft);
     dfree(h->d_flux); dfree(h->d_flag); dfree(h->slotE); dfree(h->slotH);
     dfree(h->d_hinc); dfree(h->d_einc); dfree(h->d_phE); dfree(h->d_phH);
@@ -400,11 +404,12 @@ void IncidentGen::step(float* hinc, float* einc) {
 // --------------------------------------------------------------------------
 extern "C" {
 
-int fdtd_create(const fdtd_grid* grid, const uint8_t* labels, const fdtd_material* table,
-                int32_t n_labels, const fdtd_source* source, void* cuda_stream,
-                fdtd_handle** out) {
+static int create_impl(const fdtd_grid* grid, const uint8_t* labels, const fdtd_material* table,
+                       int32_t n_labels, const double* eps_map, const double* sig_map,
+                       const fdtd_source* source, void* cuda_stream, fdtd_handle** out) {
     if (out) *out = nullptr;
-    if (!grid || !labels || !table || !source || !out) {
+    const bool maps = (eps_map != nullptr);
+    if (!grid || !source || !out || (maps ? !sig_map : (!labels || !table))) {
         g_create_err = "fdtd_create: null argument";
         return FDTD_EINVAL;
     }
@@ -412,7 +417,14 @@ int fdtd_create(const fdtd_grid* grid, const uint8_t* labels, const fdtd_materia
     try {
         h->g = *grid;
         h->src = *source;
+        h->maps = maps;
+        if (maps) {
+            static const fdtd_material air = {1.0, 0.0};
+            table = &air;
+            n_labels = 1;
+        }
         h->n_labels = n_labels;
+        h->table.assign(table, table + n_labels);
         const fdtd_grid& g = h->g;
         REQUIRE(g.nx >= 1 && g.ny >= 8, "grid: need nx >= 1 and ny >= 8");
         REQUIRE((int64_t)g.nx * g.ny < ((int64_t)1 << 31), "grid: more than 2^31 cells");
@@ -470,8 +482,9 @@ int fdtd_create(const fdtd_grid* grid, const uint8_t* labels, const fdtd_materia
             dalloc(h, &h->psiH[i], prow);
         }
         dalloc(h, &h->labels, (size_t)h->lpitch * g.ny);
-        CK(cudaMemcpy2DAsync(h->labels, h->lpitch, labels, g.nx, g.nx, g.ny, cudaMemcpyDefault,
-                             h->stream));
+        if (!maps)
+            CK(cudaMemcpy2DAsync(h->labels, h->lpitch, labels, g.nx, g.nx, g.ny, cudaMemcpyDefault,
+                                 h->stream));
         dalloc(h, &h->coef, 256);
         CK(cudaMemcpyAsync(h->coef, coef.data(), n_labels * sizeof(float2), cudaMemcpyHostToDevice,
                            h->stream));
@@ -512,10 +525,37 @@ int fdtd_create(const fdtd_grid* grid, const uint8_t* labels, const fdtd_materia
         CK(cudaStreamSynchronize(h->stream));
         cudaFree(d_max);
         REQUIRE(maxl < n_labels, "labels: a label value is >= n_labels");
-        if (source->kind != 2) {
+        if (source->kind != 2 && !maps) {
             for (uint8_t v : rows)
                 REQUIRE(table[v].n == 1.0 && table[v].k == 0.0,
                         "labels: rows tfsf_row-1 and tfsf_row must be air (n = 1, k = 0)");
+        }
+        if (maps) {
+            // per-cell coefficients from eps_r, sigma (FP64 on the host)
+            const size_t cells = (size_t)g.nx * g.ny;
+            std::vector<double> he(cells), hs(cells);
+            CK(cudaMemcpy(he.data(), eps_map, cells * sizeof(double), cudaMemcpyDefault));
+            CK(cudaMemcpy(hs.data(), sig_map, cells * sizeof(double), cudaMemcpyDefault));
+            std::vector<float2> cc((size_t)h->pitch * g.ny, make_float2(1.0f, (float)h->S));
+            for (int j = 0; j < g.ny; ++j)
+                for (int i = 0; i < g.nx; ++i) {
+                    const double eps = he[(size_t)j * g.nx + i], sig = hs[(size_t)j * g.nx + i];
+                    REQUIRE(eps > 0 && sig >= 0 && std::isfinite(eps) && std::isfinite(sig),
+                            "maps: need eps_r > 0 and sigma >= 0 in every cell");
+                    if (source->kind != 2 && (j == g.tfsf_row - 1 || j == g.tfsf_row))
+                        REQUIRE(eps == 1.0 && sig == 0.0,
+                                "maps: rows tfsf_row-1 and tfsf_row must be air (eps_r = 1, sigma = 0)");
+                    const double beta = sig * g.dt / (2.0 * kEps0 * eps);
+                    cc[(size_t)j * h->pitch + i] =
+                        make_float2((float)((1.0 - beta) / (1.0 + beta)),
+                                    (float)(h->S / (eps * (1.0 + beta))));
+                }
+            dalloc(h, &h->cellcoef, cc.size());
+            CK(cudaMemcpy(h->cellcoef, cc.data(), cc.size() * sizeof(float2), cudaMemcpyHostToDevice));
+            dalloc(h, &h->cell_eps, cells);
+            dalloc(h, &h->cell_sig, cells);
+            CK(cudaMemcpy(h->cell_eps, he.data(), cells * sizeof(double), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(h->cell_sig, hs.data(), cells * sizeof(double), cudaMemcpyHostToDevice));
         }
 
         IncidentGen& gen = h->gen;
@@ -531,6 +571,27 @@ int fdtd_create(const fdtd_grid* grid, const uint8_t* labels, const fdtd_materia
         delete h;
         return f.code;
     }
+}
+
+int fdtd_create(const fdtd_grid* grid, const uint8_t* labels, const fdtd_material* table,
+                int32_t n_labels, const fdtd_source* source, void* cuda_stream,
+                fdtd_handle** out) {
+    if (!labels || !table) {
+        if (out) *out = nullptr;
+        g_create_err = "fdtd_create: null argument";
+        return FDTD_EINVAL;
+    }
+    return create_impl(grid, labels, table, n_labels, nullptr, nullptr, source, cuda_stream, out);
+}
+
+int fdtd_create_maps(const fdtd_grid* grid, const double* eps_r, const double* sigma,
+                     const fdtd_source* source, void* cuda_stream, fdtd_handle** out) {
+    if (!eps_r || !sigma) {
+        if (out) *out = nullptr;
+        g_create_err = "fdtd_create_maps: null argument";
+        return FDTD_EINVAL;
+    }
+    return create_impl(grid, nullptr, nullptr, 0, eps_r, sigma, source, cuda_stream, out);
 }
 
 int fdtd_run(fdtd_handle* h, int64_t steps) {

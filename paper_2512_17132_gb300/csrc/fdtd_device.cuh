@@ -60,6 +60,7 @@ struct StepArgs {
     float S;              // Courant number c0 dt / dx
     const uint8_t* labels;
     const float2* coef;   // (ca, cb) per label
+    const float2* cellcoef;  // (ca, cb) per cell (pitch floats2 per row) or null
     const float* pml_e;   // [3][2P]: b, c, 1/kappa for Ez rows (top 0..P-1, then bottom)
     const float* pml_h;   // [3][2P]: same for Hx rows
     const float* hinc;    // incident eta0*Hx at edge tfsf_row, per absolute step

@@ -109,6 +109,7 @@ void produce_tables(fdtd_handle* h, int64_t upto);
 int sm_count(fdtd_handle* h);
 void sync_all(fdtd_handle* h);
 std::vector<int> segment_bounds(const fdtd_grid& g, int seg, int min_seg);
+BlockPlan& get_plan(fdtd_handle* h, int K);
 
 }  // namespace fdtd
 
@@ -130,6 +131,18 @@ struct fdtd_handle {
     int cur = 0;
     uint8_t* labels = nullptr;
     float2* coef = nullptr;
+    // per-cell materials (fdtd_create_maps): coefficients and eps_r, sigma
+    bool maps = false;
+    float2* cellcoef = nullptr;
+    double* cell_eps = nullptr;
+    double* cell_sig = nullptr;
+    std::vector<fdtd_material> table;   // per-label materials (label handles)
+    // adjoint: checkpoints of the last fdtd_forward_checkpointed run
+    std::vector<float*> ck;             // state at steps 0, every, 2 every, ...
+    size_t ck_floats = 0;
+    int64_t adj_steps = 0;
+    int adj_every = 0;
+    bool adj_valid = false;
     float* pml_e = nullptr;
     float* pml_h = nullptr;
     double2* dft = nullptr;

@@ -19,7 +19,7 @@ __global__ void k_naive_e(StepArgs a, float* __restrict__ ez, const float* __res
     const float hxb = (j + 1 < a.ny) ? hx[o + a.pitch] : 0.0f;         // Hx[ny] = 0
     float dhx = __fsub_rn(hxb, hx[o]);
     if (j == a.js) dhx = __fsub_rn(dhx, a.hinc[n]);                    // TF cell sees total Hx
-    const float2 c = a.coef[a.labels[(size_t)j * a.lpitch + i]];
+    const float2 c = a.cellcoef ? a.cellcoef[o] : a.coef[a.labels[(size_t)j * a.lpitch + i]];
     const float e = ez[o];
     const int pj = pml_e_index(j, a.ny, a.P);
     if (pj >= 0) {

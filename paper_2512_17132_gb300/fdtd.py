@@ -79,6 +79,10 @@ def load_library(path: str = LIB_PATH):
         "fdtd_get_stats": (C.c_int, [vp, C.POINTER(fdtd_stats)]),
         "fdtd_last_error": (C.c_char_p, [vp]),
         "fdtd_destroy": (None, [vp]),
+        "fdtd_create_maps": (C.c_int, [C.POINTER(fdtd_grid), vp, vp, C.POINTER(fdtd_source), vp,
+                                       C.POINTER(vp)]),
+        "fdtd_forward_checkpointed": (C.c_int, [vp, i64, i32]),
+        "fdtd_backward": (C.c_int, [vp, C.c_double, C.c_double, vp, vp, vp, dp]),
         "fdtd_autotune": (C.c_int, [vp, i32]),
         "fdtd_batch_create": (C.c_int, [C.POINTER(vp), i32, C.POINTER(vp)]),
         "fdtd_batch_set_option": (C.c_int, [vp, i32, i64]),
@@ -142,6 +146,43 @@ def fdtd_create(grid: fdtd_grid, labels, materials, source: fdtd_source, stream=
                            C.byref(out))
     _check(code, None)
     return out
+
+
+def fdtd_create_maps(grid: fdtd_grid, eps_r, sigma, source: fdtd_source, stream=None):
+    """eps_r, sigma: (ny, nx) float64 numpy arrays or device tensors."""
+    lib = load_library()
+    if not hasattr(eps_r, "data_ptr"):
+        eps_r = np.ascontiguousarray(eps_r, dtype=np.float64)
+    if not hasattr(sigma, "data_ptr"):
+        sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+    out = C.c_void_p()
+    st = C.c_void_p(stream) if isinstance(stream, int) else (
+        C.c_void_p(stream.cuda_stream) if stream is not None else None)
+    _check(lib.fdtd_create_maps(C.byref(grid), _ptr(eps_r), _ptr(sigma), C.byref(source), st,
+                                C.byref(out)), None)
+    return out
+
+
+def fdtd_forward_checkpointed(h, steps: int, every: int):
+    _check(load_library().fdtd_forward_checkpointed(h, int(steps), int(every)), h)
+
+
+def fdtd_backward(h, wR: float, wT: float, ny: int, nx: int, n_labels: int = 0, out=None):
+    """Returns dict(J, R, T, g_eps, g_sigma[, g_n, g_k]); `out` may hold
+    (g_eps, g_sigma) device tensors to fill instead of host arrays."""
+    if out is None:
+        ge = np.empty((ny, nx), dtype=np.float64)
+        gs = np.empty((ny, nx), dtype=np.float64)
+    else:
+        ge, gs = out
+    gl = np.zeros(2 * n_labels, dtype=np.float64) if n_labels else None
+    jrt = (C.c_double * 3)()
+    _check(load_library().fdtd_backward(h, float(wR), float(wT), _ptr(ge), _ptr(gs),
+                                        _ptr(gl), jrt), h)
+    res = {"J": jrt[0], "R": jrt[1], "T": jrt[2], "g_eps": ge, "g_sigma": gs}
+    if gl is not None:
+        res["g_n"], res["g_k"] = gl[0::2].copy(), gl[1::2].copy()
+    return res
 
 
 def fdtd_run(h, steps: int):
@@ -341,10 +382,14 @@ class Simulation:
     the fields of fdtd_inputs.RunSpec)."""
 
     def __init__(self, spec, stream=None, kernel: int = KERNEL_AUTO, block_steps=None,
-                 seg_rows=None, timing=False, labels=None):
+                 seg_rows=None, timing=False, labels=None, eps_r=None, sigma=None):
         self.spec = spec
-        lab = spec.labels if labels is None else labels
-        self.h = fdtd_create(make_grid(spec), lab, spec.materials, make_source(spec), stream)
+        self._maps = eps_r is not None
+        if eps_r is not None:
+            self.h = fdtd_create_maps(make_grid(spec), eps_r, sigma, make_source(spec), stream)
+        else:
+            lab = spec.labels if labels is None else labels
+            self.h = fdtd_create(make_grid(spec), lab, spec.materials, make_source(spec), stream)
         try:
             if kernel:
                 fdtd_set_option(self.h, FDTD_OPT_KERNEL, kernel)
@@ -365,6 +410,12 @@ class Simulation:
     def reset(self):
         fdtd_reset(self.h)
         return self
+
+    def gradient(self, steps, wR=1.0, wT=0.0, every=500):
+        """Forward with checkpoints, then the discrete adjoint of wR R + wT T."""
+        fdtd_forward_checkpointed(self.h, steps, every)
+        n_lab = 0 if getattr(self, "_maps", False) else len(self.spec.materials)
+        return fdtd_backward(self.h, wR, wT, self.spec.ny, self.spec.nx, n_lab)
 
     def flux(self):
         return fdtd_flux(self.h)
