@@ -41,7 +41,7 @@ def parse_args():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4"])
+    p.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
     p.add_argument("--fdtd-steps", type=int, default=0,
                    help="leapfrog steps per run (default: the config's own count)")
     p.add_argument("--kernel", type=int, default=0)
@@ -329,12 +329,67 @@ def run_c4(args):
     return 0
 
 
+def run_c5(args):
+    """Config 5: gradient of R(550 nm) on the config-1 stack at 1000 x 6000
+    cells, 30 000 steps, checkpoints every 500 steps: the checkpointed forward
+    and the discrete adjoint (segment recompute + reverse steps) timed
+    separately, as Gcell-updates/s of forward and of reverse steps."""
+    import torch
+    import fdtd_inputs as fi
+    torch.cuda.set_device(0)
+    from paper_2512_17132_gb300 import build as b
+    b.build()
+    from paper_2512_17132_gb300 import fdtd
+    spec = fi.config_c5(steps=args.fdtd_steps or 30000)
+    cells = spec.nx * spec.ny * spec.steps
+    sim = fdtd.Simulation(spec)
+    fdtd.fdtd_forward_checkpointed(sim.h, min(2000, spec.steps), 500)   # warm-up
+    fdtd.fdtd_backward(sim.h, 1.0, 0.0, spec.ny, spec.nx, len(spec.materials))
+    clocks = ClockSampler(_device_id())
+    t_f, t_b = [], []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fdtd.fdtd_forward_checkpointed(sim.h, spec.steps, 500)
+        R, T = sim.flux()
+        t1 = time.perf_counter()
+        g = fdtd.fdtd_backward(sim.h, 1.0, 0.0, spec.ny, spec.nx, len(spec.materials))
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        t_f.append(t1 - t0)
+        t_b.append(t2 - t1)
+    clk = clocks.stop()
+    st = sim.stats()
+    sim.close()
+    tf, tb = statistics.median(t_f), statistics.median(t_b)
+    line = {
+        "metric": METRIC, "value": cells / tb / 1e9, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": 1, "ms_per_step": (tf + tb) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"config 5: config-1 stack at {spec.nx}x{spec.ny}, "
+                               f"{spec.steps} steps, dR(550 nm)/d(eps_r, sigma, n, k), "
+                               "checkpoints every 500 steps",
+                   "value_is": "adjoint (backward) Gcell-updates/s: reverse steps incl. the "
+                               "segment recompute"},
+        "forward": {"value": cells / tf / 1e9, "unit": UNIT, "ms": tf * 1e3,
+                    "note": "checkpointed forward (blocked kernel + state copies)"},
+        "adjoint": {"value": cells / tb / 1e9, "unit": UNIT, "ms": tb * 1e3},
+        "R": R, "T": T, "dR_dn": list(g["g_n"]), "dR_dk": list(g["g_k"]),
+        "clocks": clk, "gpu_launches": int(st["total_launches"]),
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.config == "c4":
         return run_c4(args)
+    if args.config == "c5":
+        return run_c5(args)
     world, rank, local = dist_setup(args)
     import torch
     if world > 1:

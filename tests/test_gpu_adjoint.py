@@ -103,3 +103,62 @@ def test_backward_needs_a_checkpointed_forward(fd):
         s.run(1)
         with pytest.raises(fd.FDTDError):
             fd.fdtd_backward(s.h, 1.0, 0.0, spec.ny, spec.nx)
+
+
+def test_autograd_functions(fd):
+    import torch
+    from oracle.adjoint import maps_from_labels, objective_and_gradient
+    from paper_2512_17132_gb300.autograd import (reflectance_transmittance,
+                                                 reflectance_transmittance_table)
+    spec = _small()
+    eps, sig = maps_from_labels(spec)
+    e = torch.tensor(eps, requires_grad=True)
+    s = torch.tensor(sig, requires_grad=True)
+    rt = reflectance_transmittance(e, s, spec, 160, 40)
+    loss = 0.6 * rt[0] - 0.4 * rt[1]
+    loss.backward()
+    ref = objective_and_gradient(spec, 160, 0.6, -0.4, eps_r=eps, sigma=sig)
+    assert _close(e.grad.numpy(), ref["g_eps"]) and _close(s.grad.numpy(), ref["g_sigma"])
+    tab = torch.tensor(spec.materials, requires_grad=True)
+    rt = reflectance_transmittance_table(tab, spec, 160, 40)
+    (rt[0] + 2.0 * rt[1]).backward()
+    ref = objective_and_gradient(spec, 160, 1.0, 2.0)
+    g = tab.grad.numpy()
+    assert np.abs(g[1:, 0] - ref["g_n"][1:]).max() <= TOL * np.abs(ref["g_n"][1:]).max()
+    assert np.abs(g[1:, 1] - ref["g_k"][1:]).max() <= TOL * np.abs(ref["g_k"][1:]).max()
+
+
+def test_label_gradients_match_finite_differences_full_config5(fd):
+    """Config 5 at full size (1000 x 6000, 30 000 steps, R at 550 nm): the
+    adjoint's per-label gradients against central differences of the FP32
+    forward (Richardson-extrapolated from steps h and h/2, h = 2e-3 for n and
+    5e-4 for kappa: R oscillates with the slab's optical thickness, so the
+    plain h^2 term is not negligible). These steps keep the change of R far above the FP32
+    noise of a 1.8e11-update run (a one-cell step of 1e-4 would change R by
+    ~1e-9, below FP32 resolution; per-cell gradients are checked against
+    the FP64 oracle adjoint on the 128 x 512 crop instead)."""
+    spec = config_c5()
+    with fd.Simulation(spec) as s:
+        g = s.gradient(spec.steps, 1.0, 0.0, 500)
+    h = 2e-3
+
+    def R_at(l, col, dv):
+        m = spec.materials.copy()
+        m[l, col] += dv
+        with fd.Simulation(spec.with_(materials=m)) as s:
+            s.run(spec.steps)
+            return s.flux()[0]
+
+    def fd_at(l, col, hh):
+        if spec.materials[l, col] >= 2 * hh:                 # central difference
+            return (R_at(l, col, hh) - R_at(l, col, -hh)) / (2 * hh)
+        # kappa = 0: one-sided second-order difference
+        return (-3 * R_at(l, col, 0.0) + 4 * R_at(l, col, hh) - R_at(l, col, 2 * hh)) / (2 * hh)
+
+    for l in (1, 2):
+        for col, key in ((0, "g_n"), (1, "g_k")):
+            hh = h if col == 0 else h / 4       # kappa: smaller step, R is curved near kappa = 0
+            # Richardson extrapolation of two O(h^2) estimates: error O(h^4)
+            fdv = (4.0 * fd_at(l, col, hh / 2) - fd_at(l, col, hh)) / 3.0
+            print(f"label {l} {key}: adjoint {g[key][l]:.6e} fd {fdv:.6e}")
+            assert abs(g[key][l] - fdv) <= 1e-3 * max(abs(fdv), 1e-2), (l, key)
