@@ -9,11 +9,14 @@
 // reverse, the transpose of every update of the leapfrog step:
 //
 //   forward step n                         reverse step n
-//   Ez <- ca Ez + cb curl(H, psi_E)        H monitor sources; transpose of the
-//   Hx, Hy <- H + S dEz (+ psi_H)          H updates (psi_H carry); E monitor
-//   DFTs of Ez and averaged Hx             source; gca += lE Ez^{n-1/2},
-//                                          gcb += lE curl^n; transpose of the
-//                                          E update (psi_E carry), lE <- ca lE
+//   Ez <- ca Ez + cb curl(H, psi_E)        k_adj_h: H monitor sources, transposes
+//   Hx, Hy <- H + S dEz (+ psi_H)          of the H updates (psi_H carry), E
+//   DFTs of Ez and averaged Hx             monitor source; k_adj_e: gca += lE
+//                                          Ez^{n-1/2}, gcb += lE curl^n, transpose
+//                                          of the E update (psi_E carry), ca lE
+//
+// Each reverse kernel recomputes the neighbour terms it needs instead of
+// staging them, so the adjoint of Ez and the CPML carries are ping-ponged.
 //
 // in the library's units (Ez, eta0 H; ca, cb of Sec. 2.3). The monitor
 // sources follow from J = wR R + wT T with R, T the Poynting ratios of
@@ -60,9 +63,8 @@ struct AdjArgs {
     const double2* phH;
     const double2* dft;     // final DFT sums [4][nx]
     double kR, kT;          // dJ/d Re(E conj H) per monitor row
-    float* lE; float* lX; float* lY;
-    float* mE; float* mH;   // CPML carries [2P][pitch]
-    float* D; float* C; float* DX;
+    float* lE;              // adjoint of Ez (the buffer the H reverse updates)
+    float* lX; float* lY;
     float* gA; float* gB;   // FP32 per-segment sums
     const float* tE; const float* tX; const float* tY; const float* tPE;   // tape state of step n
 };
@@ -101,56 +103,75 @@ __device__ __forceinline__ float src_e(const AdjArgs& a, int j, int i, int64_t n
     return (float)s;
 }
 
-// transpose of the Hx update (with the psi_H carry) and the H monitor source
-__global__ void k_adj_h1(AdjArgs a, int64_t n) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y;
-    if (i >= a.nx) return;
+// adjoint of d_ez at edge j (transpose of the Hx update, psi_H carry read
+// from mH_in); x is the adjoint of Hx^{n+1} including its monitor source
+__device__ __forceinline__ float adj_dez(const AdjArgs& a, int j, int i, int64_t n,
+                                         const float* mH_in, float* mH_out) {
+    if (j <= 0 || j >= a.ny) return 0.f;
     const size_t o = (size_t)j * a.pitch + i;
     float x = a.lX[o];
-    if (j == a.jr || j == a.jr + 1 || j == a.jt || j == a.jt + 1) {
-        x = __fadd_rn(x, src_h(a, j, i, n));
-        a.lX[o] = x;
+    if (j == a.jr || j == a.jr + 1 || j == a.jt || j == a.jt + 1) x = __fadd_rn(x, src_h(a, j, i, n));
+    const int ph = pml_h_index(j, a.ny, a.P);
+    if (ph >= 0) {
+        const size_t q = (size_t)ph * a.pitch + i;
+        const float sx = __fmul_rn(a.S, x);
+        const float nu = __fadd_rn(sx, mH_in[q]);
+        if (mH_out) mH_out[q] = __fmul_rn(a.pml_h[ph], nu);
+        return __fmaf_rn(a.pml_h[2 * a.P + ph], nu, __fmul_rn(sx, a.pml_h[4 * a.P + ph]));
     }
-    float d = 0.f;
-    if (j > 0) {
-        const int ph = pml_h_index(j, a.ny, a.P);
-        if (ph >= 0) {
-            float* m = a.mH + (size_t)ph * a.pitch + i;
-            const float sx = __fmul_rn(a.S, x);
-            const float nu = __fadd_rn(sx, *m);
-            d = __fmaf_rn(a.pml_h[2 * a.P + ph], nu, __fmul_rn(sx, a.pml_h[4 * a.P + ph]));
-            *m = __fmul_rn(a.pml_h[ph], nu);
-        } else {
-            d = __fmul_rn(a.S, x);
-        }
-    }
-    a.D[o] = d;
+    return __fmul_rn(a.S, x);
 }
 
-// adjoint of Ez^{n+1/2}: carried part + Hy and Hx transposes + E monitor source
-__global__ void k_adj_h2(AdjArgs a, int64_t n) {
+// Reverse of the H half-step: the adjoint of Ez^{n+1/2} collects the carried
+// part, the transposes of both H updates and the E monitor source.
+__global__ void k_adj_h(AdjArgs a, int64_t n, const float* __restrict__ mH_in,
+                        float* __restrict__ mH_out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
     if (i >= a.nx) return;
     const size_t o = (size_t)j * a.pitch + i;
     const int ir = (i + 1 == a.nx) ? 0 : i + 1;
+    const float d0 = adj_dez(a, j, i, n, mH_in, mH_out);
+    const float d1 = adj_dez(a, j + 1, i, n, mH_in, nullptr);
     float e = a.lE[o];
     e = __fadd_rn(e, __fmul_rn(a.S, __fsub_rn(a.lY[o], a.lY[(size_t)j * a.pitch + ir])));
-    const float dn = (j + 1 < a.ny) ? a.D[o + a.pitch] : 0.f;
-    e = __fadd_rn(e, __fsub_rn(a.D[o], dn));
+    e = __fadd_rn(e, __fsub_rn(d0, d1));
     if (j == a.jr || j == a.jt) e = __fadd_rn(e, src_e(a, j, i, n));
     a.lE[o] = e;
 }
 
-// gradient sums and the transpose of the Ez update (with the psi_E carry)
-__global__ void k_adj_e1(AdjArgs a, int64_t n) {
+// adjoint of curl (cbar) and of d_hx (psi_E carry from mE_in) at cell (j, i)
+__device__ __forceinline__ void adj_curl(const AdjArgs& a, int j, int i, const float* lE_in,
+                                         const float* mE_in, float* mE_out, float* cbar,
+                                         float* ghx) {
+    const size_t o = (size_t)j * a.pitch + i;
+    const float2 c = cell_coef(a, j, i);
+    const float cb = __fmul_rn(c.y, lE_in[o]);
+    *cbar = cb;
+    const int pe = pml_e_index(j, a.ny, a.P);
+    if (pe >= 0) {
+        const size_t q = (size_t)pe * a.pitch + i;
+        const float rho = __fadd_rn(cb, mE_in[q]);
+        if (mE_out) mE_out[q] = __fmul_rn(a.pml_e[pe], rho);
+        *ghx = __fmaf_rn(a.pml_e[2 * a.P + pe], rho, __fmul_rn(cb, a.pml_e[4 * a.P + pe]));
+    } else {
+        *ghx = cb;
+    }
+}
+
+// Reverse of the E half-step: gradient sums, transposes of d_hy and d_hx
+// into the H adjoints (with the H monitor source made persistent) and
+// lE <- ca lE into the other adjoint buffer.
+__global__ void k_adj_e(AdjArgs a, int64_t n, const float* __restrict__ lE_in,
+                        float* __restrict__ lE_out, const float* __restrict__ mE_in,
+                        float* __restrict__ mE_out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
     if (i >= a.nx) return;
     const size_t o = (size_t)j * a.pitch + i;
     const int ir = (i + 1 == a.nx) ? 0 : i + 1;
-    const float eb = a.lE[o];
+    const int il = (i == 0) ? a.nx - 1 : i - 1;
+    const float eb = lE_in[o];
     // forward curl of step n from the taped state (same rounding as forward)
     const float dhy = __fsub_rn(a.tY[(size_t)j * a.pitch + ir], a.tY[o]);
     const float hxb = (j + 1 < a.ny) ? a.tX[o + a.pitch] : 0.0f;
@@ -158,38 +179,24 @@ __global__ void k_adj_e1(AdjArgs a, int64_t n) {
     if (j == a.js) dhx = __fsub_rn(dhx, a.hinc[n]);
     const int pe = pml_e_index(j, a.ny, a.P);
     float curl;
-    const float2 c = cell_coef(a, j, i);
-    const float cbar = __fmul_rn(c.y, eb);
-    float gx;
     if (pe >= 0) {
         const float b = a.pml_e[pe], cc = a.pml_e[2 * a.P + pe], ik = a.pml_e[4 * a.P + pe];
         const float psi = psi_new(b, cc, a.tPE[(size_t)pe * a.pitch + i], dhx);
         curl = __fadd_rn(dhy, __fmaf_rn(dhx, ik, psi));
-        float* m = a.mE + (size_t)pe * a.pitch + i;
-        const float rho = __fadd_rn(cbar, *m);
-        gx = __fmaf_rn(cc, rho, __fmul_rn(cbar, ik));
-        *m = __fmul_rn(b, rho);
     } else {
         curl = __fadd_rn(dhy, dhx);
-        gx = cbar;
     }
     a.gA[o] = __fmaf_rn(eb, a.tE[o], a.gA[o]);
     a.gB[o] = __fmaf_rn(eb, curl, a.gB[o]);
-    a.C[o] = cbar;
-    a.DX[o] = gx;
-    a.lE[o] = __fmul_rn(c.x, eb);
-}
-
-// transposes of d_hy = Hy[i+1] - Hy[i] and d_hx = Hx[j+1] - Hx[j]
-__global__ void k_adj_e2(AdjArgs a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y;
-    if (i >= a.nx) return;
-    const size_t o = (size_t)j * a.pitch + i;
-    const int il = (i == 0) ? a.nx - 1 : i - 1;
-    a.lY[o] = __fadd_rn(a.lY[o], __fsub_rn(a.C[(size_t)j * a.pitch + il], a.C[o]));
-    const float up = (j > 0) ? a.DX[o - a.pitch] : 0.f;
-    a.lX[o] = __fadd_rn(a.lX[o], __fsub_rn(up, a.DX[o]));
+    float c0, g0, cl, gl, gu = 0.f, dummy;
+    adj_curl(a, j, i, lE_in, mE_in, mE_out, &c0, &g0);
+    adj_curl(a, j, il, lE_in, mE_in, nullptr, &cl, &dummy);
+    if (j > 0) adj_curl(a, j - 1, i, lE_in, mE_in, nullptr, &dummy, &gu);
+    a.lY[o] = __fadd_rn(a.lY[o], __fsub_rn(cl, c0));
+    float x = a.lX[o];
+    if (j == a.jr || j == a.jr + 1 || j == a.jt || j == a.jt + 1) x = __fadd_rn(x, src_h(a, j, i, n));
+    a.lX[o] = __fadd_rn(x, __fsub_rn(gu, g0));
+    lE_out[o] = __fmul_rn(cell_coef(a, j, i).x, eb);
 }
 
 __global__ void k_adj_flush(float* gA, float* gB, double* GA, double* GB, int nx, int ny,
@@ -402,9 +409,9 @@ int fdtd_backward(fdtd_handle* h, double wR, double wT, double* g_eps, double* g
         const size_t sf = state_floats(h);
         tape.assign((size_t)std::min<int64_t>(every, steps), nullptr);
         for (auto& t : tape) ACK(cudaMalloc(&t, sf * sizeof(float)));
-        // lE lX lY D C DX gA gB (f each) + mE mH (pr each)
-        ACK(cudaMalloc(&buf, (8 * f + 2 * pr) * sizeof(float)));
-        ACK(cudaMemsetAsync(buf, 0, (8 * f + 2 * pr) * sizeof(float), h->stream));
+        // lE[2] lX lY gA gB (f each) + mE[2] mH[2] (pr each)
+        ACK(cudaMalloc(&buf, (6 * f + 4 * pr) * sizeof(float)));
+        ACK(cudaMemsetAsync(buf, 0, (6 * f + 4 * pr) * sizeof(float), h->stream));
         ACK(cudaMalloc(&dbl, 2 * f * sizeof(double)));
         ACK(cudaMemsetAsync(dbl, 0, 2 * f * sizeof(double), h->stream));
         ACK(cudaMalloc(&dummy, (size_t)4 * nx * sizeof(double2)));
@@ -416,9 +423,11 @@ int fdtd_backward(fdtd_handle* h, double wR, double wT, double* g_eps, double* g
         a.phE = h->d_phE; a.phH = h->d_phH; a.dft = h->dft;
         a.kR = wR / (-(double)nx * s0);
         a.kT = wT / ((double)nx * s0);
-        a.lE = buf; a.lX = buf + f; a.lY = buf + 2 * f; a.D = buf + 3 * f; a.C = buf + 4 * f;
-        a.DX = buf + 5 * f; a.gA = buf + 6 * f; a.gB = buf + 7 * f;
-        a.mE = buf + 8 * f; a.mH = buf + 8 * f + pr;
+        float* lEb[2] = {buf, buf + f};
+        a.lX = buf + 2 * f; a.lY = buf + 3 * f; a.gA = buf + 4 * f; a.gB = buf + 5 * f;
+        float* mEb[2] = {buf + 6 * f, buf + 6 * f + pr};
+        float* mHb[2] = {buf + 6 * f + 2 * pr, buf + 6 * f + 3 * pr};
+        int pe_cur = 0, ph_cur = 0, le_cur = 0;
         double* GA = dbl;
         double* GB = dbl + f;
         const dim3 blk(256), grd((nx + 255) / 256, ny);
@@ -434,13 +443,16 @@ int fdtd_backward(fdtd_handle* h, double wR, double wT, double* g_eps, double* g
                 const int64_t n = c0 + m;
                 const StateView v = view(h, tape[m]);
                 a.tE = v.E; a.tX = v.X; a.tY = v.Y; a.tPE = v.PE;
-                k_adj_h1<<<grd, blk, 0, h->stream>>>(a, n);
-                k_adj_h2<<<grd, blk, 0, h->stream>>>(a, n);
-                k_adj_e1<<<grd, blk, 0, h->stream>>>(a, n);
-                k_adj_e2<<<grd, blk, 0, h->stream>>>(a);
+                a.lE = lEb[le_cur];
+                k_adj_h<<<grd, blk, 0, h->stream>>>(a, n, mHb[ph_cur], mHb[ph_cur ^ 1]);
+                ph_cur ^= 1;
+                k_adj_e<<<grd, blk, 0, h->stream>>>(a, n, lEb[le_cur], lEb[le_cur ^ 1],
+                                                    mEb[pe_cur], mEb[pe_cur ^ 1]);
+                pe_cur ^= 1;
+                le_cur ^= 1;
             }
             k_adj_flush<<<grd, blk, 0, h->stream>>>(a.gA, a.gB, GA, GB, nx, ny, pitch);
-            h->total_launches += 4 * L + 1;
+            h->total_launches += 2 * L + 1;
             ACK(cudaGetLastError());
         }
         // chain rule to (eps_r, sigma) per cell and (n, kappa) per label
