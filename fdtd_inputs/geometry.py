@@ -33,6 +33,14 @@ def stack_labels(nx: int, ny: int, layers) -> np.ndarray:
     return lab
 
 
+def cylinder_array_labels(nx: int, ny: int, radius_cells: float) -> np.ndarray:
+    """One period of a cylinder array: a disc of label 1 centred in the
+    middle row of a periodic strip of nx columns."""
+    jj, ii = np.mgrid[0:ny, 0:nx]
+    inside = (ii + 0.5 - nx / 2.0) ** 2 + (jj + 0.5 - ny / 2.0) ** 2 <= radius_cells ** 2
+    return inside.astype(np.uint8)
+
+
 def c1_labels(nx: int = 256) -> np.ndarray:
     """Config 1: air / cuticle rows 40-89 (label 1) / slab rows 90-214 (label 2)."""
     return stack_labels(nx, 256, [(*C1_ROWS["cuticle"], 1), (*C1_ROWS["slab"], 2)])

@@ -119,9 +119,9 @@ void ensure_tables(fdtd_handle* h, int64_t n_end) {
     h->gen.reset(plan);
 }
 
-// Compute table entries up to step `upto` and queue their upload.
-void produce_tables(fdtd_handle* h, int64_t upto) {
-    const int64_t from = h->tab_uploaded;
+// Host part: compute incident and phase table entries up to step `upto`
+// into the pinned buffers (no CUDA calls; handles may run in parallel).
+void compute_tables(fdtd_handle* h, int64_t upto) {
     while (h->gen.m < upto) {
         const int64_t m = h->gen.m;
         float hv, ev;
@@ -133,6 +133,11 @@ void produce_tables(fdtd_handle* h, int64_t upto) {
         h->h_phE[m] = make_double2(std::cos(aE), std::sin(aE));
         h->h_phH[m] = make_double2(std::cos(aH), std::sin(aH));
     }
+}
+
+// Queue the upload of the computed entries not yet on the device.
+void upload_tables(fdtd_handle* h, int64_t upto) {
+    const int64_t from = h->tab_uploaded;
     if (upto > from) {
         const int64_t cnt = upto - from;
         CK(cudaMemcpyAsync(h->d_hinc + from, h->h_hinc + from, cnt * sizeof(float), cudaMemcpyHostToDevice, h->stream));
@@ -141,6 +146,12 @@ void produce_tables(fdtd_handle* h, int64_t upto) {
         CK(cudaMemcpyAsync(h->d_phH + from, h->h_phH + from, cnt * sizeof(double2), cudaMemcpyHostToDevice, h->stream));
         h->tab_uploaded = upto;
     }
+}
+
+// Compute table entries up to step `upto` and queue their upload.
+void produce_tables(fdtd_handle* h, int64_t upto) {
+    compute_tables(h, upto);
+    upload_tables(h, upto);
 }
 
 int sm_count(fdtd_handle* h) {

@@ -21,6 +21,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -450,10 +451,24 @@ int fdtd_batch_run(fdtd_batch* b, int64_t steps) {
         const int nl_full = launches_per_chunk(K);
         const int64_t chunk = (int64_t)nl_full * K;
         int64_t s = 0;
+        const int n_threads = (int)std::max<unsigned>(
+            1u, std::min<unsigned>((unsigned)b->hs.size(), std::thread::hardware_concurrency()));
         while (s < steps) {
             const int64_t ce = std::min(steps, s + chunk);
+            // host-side incident tables of every handle, in parallel
+            {
+                std::vector<std::thread> pool;
+                for (int t = 0; t < n_threads; ++t)
+                    pool.emplace_back([&, t]() {
+                        for (size_t q = t; q < b->hs.size(); q += n_threads) {
+                            fdtd_handle* h = b->hs[q];
+                            compute_tables(h, std::max(h->n + ce, h->tab_uploaded));
+                        }
+                    });
+                for (auto& th : pool) th.join();
+            }
             for (auto* h : b->hs) {
-                produce_tables(h, std::max(h->n + ce, h->tab_uploaded));
+                upload_tables(h, std::max(h->n + ce, h->tab_uploaded));
                 BCK(cudaEventRecord(h->ev_tab, h->stream));
                 BCK(cudaStreamWaitEvent(b->stream, h->ev_tab, 0));
             }

@@ -106,6 +106,8 @@ struct Fail {
 StepArgs step_args(fdtd_handle* h);
 void ensure_tables(fdtd_handle* h, int64_t n_end);
 void produce_tables(fdtd_handle* h, int64_t upto);
+void compute_tables(fdtd_handle* h, int64_t upto);
+void upload_tables(fdtd_handle* h, int64_t upto);
 int sm_count(fdtd_handle* h);
 void sync_all(fdtd_handle* h);
 std::vector<int> segment_bounds(const fdtd_grid& g, int seg, int min_seg);
