@@ -923,7 +923,7 @@ int fdtd_set_option(fdtd_handle* h, int32_t option, int64_t value) {
             h->opt_watchdog = value;
             return FDTD_OK;
         case FDTD_OPT_VARIANT:
-            if (value < 0 || value > 1) break;
+            if (value < 0 || value > 2) break;
             h->opt_variant = (int)value;
             return FDTD_OK;
         default:

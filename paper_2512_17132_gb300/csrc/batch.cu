@@ -34,7 +34,7 @@ struct fdtd_batch {
     int device = 0;
     cudaStream_t stream = nullptr, side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_in = nullptr;
-    int K = 8, variant = 0, seg = 0, timing = 0, use_graph = 1;
+    int K = 8, variant = 2, seg = 0, timing = 0, use_graph = 1;
     // plan
     bool planned = false;
     int pK = 0, pvar = -1, pseg = -1, seg_used = 0;
@@ -308,7 +308,7 @@ int batch_tune(fdtd_batch* b, int trials) {
     double best = -1;
     int bK = b->K, bv = b->variant, bs = 0;
     for (int K : {8, 7, 6}) {
-        for (int v : {0, 1}) {
+        for (int v : {0, 1, 2}) {
             if (K == 8 && v == 1) continue;          // exceeds the register file at K = 8
             const int s0 = model_seg(b, K, v);
             for (int f : {-1, 0, 1}) {
@@ -364,6 +364,7 @@ int fdtd_batch_create(fdtd_handle* const* hs, int32_t n, fdtd_batch** out) {
         BCK(cudaMalloc(&b->d_step_base, sizeof(int64_t)));
         configure_twin_batch();
         b->K = std::min(hs[0]->opt_block, blocked_max_K());
+        b->variant = hs[0]->opt_variant;
         *out = b;
         return FDTD_OK;
     } catch (const Fail& f) {
@@ -390,7 +391,7 @@ int fdtd_batch_set_option(fdtd_batch* b, int32_t option, int64_t value) {
             b->seg = (int)value;
             return FDTD_OK;
         case FDTD_OPT_VARIANT:
-            if (value < 0 || value > 1) break;
+            if (value < 0 || value > 2) break;
             b->variant = (int)value;
             return FDTD_OK;
         case FDTD_OPT_TIMING:
@@ -434,7 +435,7 @@ int fdtd_batch_run(fdtd_batch* b, int64_t steps) {
         if (steps == 0) return FDTD_OK;
         BCK(cudaSetDevice(b->device));
         const int K = std::min(b->K, blocked_max_K());
-        const int var = (K == 8) ? 0 : b->variant;
+        const int var = (K == 8 && b->variant == 1) ? 0 : b->variant;
         if (!b->planned || b->pK != K || b->pvar != var || b->pseg != b->seg) {
             BCK(cudaStreamSynchronize(b->stream));
             build_plan(b, K, var, b->seg);

@@ -44,6 +44,26 @@ __device__ __forceinline__ void st4(float* p, const float (&v)[4]) {
     *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
+// Asynchronous global -> shared copies (cp.async); `bytes` = 0 zero-fills the
+// destination without reading the source.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int bytes) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, int bytes) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+constexpr int kRing = 4;   // rows in flight per warp for code shape 2
+
 }  // namespace
 
 // Register state of one warp's pipeline: per level k the pending row
@@ -197,7 +217,10 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
 }
 
 // One warp task: strip `task % n_strips` of segment `task / n_strips`.
-template <int K, bool U2>
+// Code shapes V: 0 one row per loop trip with a one-row register prefetch;
+// 1 two rows per loop trip on plain stretches; 2 level-0 rows streamed
+// through a shared-memory ring filled kRing rows ahead by cp.async.
+template <int K, int V>
 __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float2* s_coef,
                                              const int task, const int64_t n0) {
     constexpr int H = ((K + 3) / 4) * 4;
@@ -245,6 +268,54 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float2*
         return f;
     };
 
+    auto finish = [&](const int t, float (&fE)[4], float (&fX)[4], float (&fY)[4]) {
+        const int ro = t - K;
+        if (ln.own && ro >= y0 && ro < y1) {
+            const size_t o = (size_t)ro * pitch + ln.gx;
+            st4(a.ez_out + o, fE);
+            st4(a.hx_out + o, fX);
+            st4(a.hy_out + o, fY);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { p.E[K][q] = fE[q]; p.X[K][q] = fX[q]; }
+    };
+
+    if (V == 2) {
+        __shared__ float4 ring[kRing][3][32];
+        __shared__ uint32_t ring_l[kRing][32];
+        auto issue = [&](const int row, const int slot) {
+            const bool ok = row < ny;
+            const size_t o = (size_t)(ok ? row : 0) * pitch + ln.gx;
+            const int nb = ok ? 16 : 0;
+            cp_async16(&ring[slot][0][lane], a.ez_in + o, nb);
+            cp_async16(&ring[slot][1][lane], a.hx_in + o, nb);
+            cp_async16(&ring[slot][2][lane], a.hy_in + o, nb);
+            cp_async4(&ring_l[slot][lane], a.s.labels + (size_t)(ok ? row : 0) * lpitch + ln.gx,
+                      ok ? 4 : 0);
+            cp_async_commit();
+        };
+#pragma unroll
+        for (int d = 0; d < kRing; ++d) issue(t_begin + d, d);
+        int slot = 0;
+#pragma unroll 1
+        for (int t = t_begin; t < t_end; ++t) {
+            cp_async_wait<kRing - 1>();
+            float fE[4], fX[4], fY[4];
+            const float4 e4 = ring[slot][0][lane], x4 = ring[slot][1][lane], y4 = ring[slot][2][lane];
+            uint32_t fL = ring_l[slot][lane];
+            fE[0] = e4.x; fE[1] = e4.y; fE[2] = e4.z; fE[3] = e4.w;
+            fX[0] = x4.x; fX[1] = x4.y; fX[2] = x4.z; fX[3] = x4.w;
+            fY[0] = y4.x; fY[1] = y4.y; fY[2] = y4.z; fY[3] = y4.w;
+            issue(t + kRing, slot);
+            slot = (slot + 1 == kRing) ? 0 : slot + 1;
+            if (is_fast(t)) advance<K, false>(p, fE, fX, fY, fL, t, a, ln, slotE, slotH, n0);
+            else advance<K, true>(p, fE, fX, fY, fL, t, a, ln, slotE, slotH, n0);
+            finish(t, fE, fX, fY);
+        }
+        cp_async_wait<0>();
+        return;
+    }
+
     // software pipeline: row t+1 is fetched while row t is processed
     float nE[4], nX[4], nY[4];
     uint32_t nL = 0u;
@@ -273,20 +344,12 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float2*
         }
         if (fast) advance<K, false>(p, fE, fX, fY, fL, t, a, ln, slotE, slotH, n0);
         else advance<K, true>(p, fE, fX, fY, fL, t, a, ln, slotE, slotH, n0);
-        const int ro = t - K;
-        if (ln.own && ro >= y0 && ro < y1) {
-            const size_t o = (size_t)ro * pitch + ln.gx;
-            st4(a.ez_out + o, fE);
-            st4(a.hx_out + o, fX);
-            st4(a.hy_out + o, fY);
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) { p.E[K][q] = fE[q]; p.X[K][q] = fX[q]; }
+        finish(t, fE, fX, fY);
     };
     int t = t_begin;
 #pragma unroll 1
     while (t < t_end) {
-        if (U2 && t + 1 < t_end && is_fast(t) && is_fast(t + 1)) {
+        if (V == 1 && t + 1 < t_end && is_fast(t) && is_fast(t + 1)) {
             iteration(t, true);
             iteration(t + 1, true);
             t += 2;
@@ -298,13 +361,13 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float2*
     }
 }
 
-template <int K, bool U2>
+template <int K, int V>
 __global__ void __launch_bounds__(32) k_blocked(const BlockedArgs a, const int64_t n0) {
     __shared__ float2 s_coef[256];
     for (int t = threadIdx.x; t < a.s.n_labels; t += blockDim.x) s_coef[t] = a.s.coef[t];
     __syncwarp();
     if ((int)blockIdx.x >= a.n_tasks) return;       // one warp per block and task
-    blocked_task<K, U2>(a, s_coef, blockIdx.x, n0);
+    blocked_task<K, V>(a, s_coef, blockIdx.x, n0);
 }
 
 // Many independent simulations in one launch: the grid covers the union of
@@ -313,7 +376,7 @@ __global__ void __launch_bounds__(32) k_blocked(const BlockedArgs a, const int64
 // and runs the same task body. The absolute step of the launch is
 // n_base(sim) + *step_base + step_off, so a captured chunk of launches can be
 // replayed with a new *step_base.
-template <int K, bool U2>
+template <int K, int V>
 __global__ void __launch_bounds__(32) k_blocked_batch(const BatchArgs b, const int step_off,
                                                       const int parity) {
     __shared__ float2 s_coef[256];
@@ -330,13 +393,13 @@ __global__ void __launch_bounds__(32) k_blocked_batch(const BatchArgs b, const i
     for (int t = threadIdx.x; t < a.s.n_labels; t += 32) s_coef[t] = a.s.coef[t];
     __syncwarp();
     const int64_t n0 = a.n_base + *b.step_base + step_off;
-    blocked_task<K, U2>(a, s_coef, task - b.first_task[sim], n0);
+    blocked_task<K, V>(a, s_coef, task - b.first_task[sim], n0);
 }
 
-template <int K, bool U2>
+template <int K, int V>
 static int occupancy_warps() {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_blocked<K, U2>, 32, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_blocked<K, V>, 32, 0) != cudaSuccess)
         return 0;
     return b;
 }
@@ -347,7 +410,10 @@ int blocked_max_K() { return 8; }
 
 int blocked_warps_per_sm(int K, int variant) {
     switch (K) {
-#define X(k) case k: return variant ? occupancy_warps<k, true>() : occupancy_warps<k, false>();
+#define X(k)                                                               \
+    case k:                                                                \
+        return variant == 2 ? occupancy_warps<k, 2>()                      \
+                            : (variant ? occupancy_warps<k, 1>() : occupancy_warps<k, 0>());
         FDTD_BLOCKED_CASES(X)
 #undef X
         default: return 0;
@@ -360,8 +426,9 @@ bool launch_blocked_batch(const BatchArgs& b, int K, int variant, int step_off, 
     switch (K) {
 #define X(k)                                                                            \
     case k:                                                                             \
-        if (variant) k_blocked_batch<k, true><<<grid, 32, 0, st>>>(b, step_off, parity); \
-        else k_blocked_batch<k, false><<<grid, 32, 0, st>>>(b, step_off, parity);        \
+        if (variant == 2) k_blocked_batch<k, 2><<<grid, 32, 0, st>>>(b, step_off, parity); \
+        else if (variant) k_blocked_batch<k, 1><<<grid, 32, 0, st>>>(b, step_off, parity); \
+        else k_blocked_batch<k, 0><<<grid, 32, 0, st>>>(b, step_off, parity);            \
         break;
         FDTD_BLOCKED_CASES(X)
 #undef X
@@ -375,8 +442,9 @@ bool launch_blocked(const BlockedArgs& a, int K, int variant, int64_t n0, cudaSt
     switch (K) {
 #define X(k)                                                                  \
     case k:                                                                   \
-        if (variant) k_blocked<k, true><<<grid, 32, 0, st>>>(a, n0);          \
-        else k_blocked<k, false><<<grid, 32, 0, st>>>(a, n0);                 \
+        if (variant == 2) k_blocked<k, 2><<<grid, 32, 0, st>>>(a, n0);        \
+        else if (variant) k_blocked<k, 1><<<grid, 32, 0, st>>>(a, n0);        \
+        else k_blocked<k, 0><<<grid, 32, 0, st>>>(a, n0);                     \
         break;
         FDTD_BLOCKED_CASES(X)
 #undef X

@@ -88,7 +88,9 @@ def test_config1b_fields_and_rt(fd, ref_c1b, kernel, K):
 
 @pytest.mark.parametrize("K,seg,variant", [(8, None, 1), (8, None, 0), (8, 25, 1), (7, 40, 0),
                                            (7, 40, 1), (5, 23, 1), (4, 31, 0), (2, 19, 1),
-                                           (1, 17, 1), (6, 200, 0), (6, 33, 1), (3, 29, 1)])
+                                           (1, 17, 1), (6, 200, 0), (6, 33, 1), (3, 29, 1),
+                                           (8, None, 2), (8, 27, 2), (7, 41, 2), (5, 19, 2),
+                                           (3, 22, 2), (1, 18, 2)])
 def test_blocked_is_bitwise_equal_to_naive(fd, K, seg, variant):
     spec = config_c1b(steps=411)
     with fd.Simulation(spec, kernel=1) as a:
