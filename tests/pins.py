@@ -105,3 +105,47 @@ def rows_to_index(ny, layers):
         for j in range(r0, r1):
             idx[j] = nk
     return idx
+
+
+def lattice_stack_rt_tez(omega, dx, dt, row_index):
+    """R and T of an x-uniform stack on the P-polarised (TEz) Yee lattice:
+    Hz at cell centres, Ex on the horizontal edges, each edge taking the
+    mean complex permittivity of the two cells it separates. Steady state
+    at e^{-i w t} (theta = w dt/2, w~ = 2 sin(theta)/dt):
+      -i w~ mu0 Hz_j = -(Ex_{j+1} - Ex_j)/dx,
+      (-i w~ eps0 eps_e + sigma_e cos(theta)) Ex_j = -(Hz_j - Hz_{j-1})/dx.
+    row_index as for lattice_stack_rt (rows 0 and 1 air; the last row's
+    medium continues below, T is None when it is not air).
+    """
+    theta = omega * dt / 2.0
+    wt = 2.0 * math.sin(theta) / dt
+    N = len(row_index)
+    eps_c = np.array([complex(nk) ** 2 for nk in row_index])
+    # edge j separates rows j-1 and j (edges 1..N-1); the mean of eps_r and
+    # sigma is the mean of the complex permittivity
+    a = np.zeros(N + 1, dtype=np.complex128)
+    for j in range(1, N):
+        e = 0.5 * (eps_c[j - 1] + eps_c[j])
+        a[j] = dx * (-1j * wt * EPS0 * e.real + e.imag * omega * EPS0 * math.cos(theta))
+    g = -1j * wt * MU0 * dx
+    k0 = lattice_wavenumber(omega, dx, dt)
+    s0 = 2j * math.sin(k0.real * dx / 2.0)
+    nb = complex(row_index[-1])
+    kb = lattice_wavenumber(omega, dx, dt, nb.real, nb.imag)
+    sb = 2j * np.sin(kb * dx / 2.0)
+    # outgoing wave in the bottom medium: Ex_j = e^{i k j dx},
+    # Hz_j = -(s/g) e^{i k (j+1/2) dx}; it holds down from edge N-1 and
+    # centre N-1, whose equations involve no averaged edge
+    Ex = np.exp(1j * kb * (N - 1) * dx)
+    Hz = -(sb / g) * np.exp(1j * kb * (N - 0.5) * dx)
+    for j in range(N - 1, 1, -1):
+        Hz = Hz + a[j] * Ex            # Hz_{j-1} from the edge-j equation
+        Ex = Ex + g * Hz               # Ex_{j-1} from the centre-(j-1) equation
+    Hz0 = Hz + a[1] * Ex               # Hz_0; Ex now holds Ex_1
+    # air: Ex_1 = A e^{i k dx} + B e^{-i k dx},
+    #      Hz_0 = -(s0/g) (A e^{i k dx/2} - B e^{-i k dx/2})
+    M = np.array([[np.exp(1j * k0 * dx), np.exp(-1j * k0 * dx)],
+                  [-(s0 / g) * np.exp(0.5j * k0 * dx), (s0 / g) * np.exp(-0.5j * k0 * dx)]])
+    A, B = np.linalg.solve(M, np.array([Ex, Hz0]))
+    T = abs(1.0 / A) ** 2 if nb == 1.0 else None
+    return abs(B / A) ** 2, T
