@@ -49,6 +49,8 @@ def parse_args():
     p.add_argument("--seg-rows", type=int, default=0)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--pol", default="s", choices=["s", "p"],
+                   help="polarisation of the runs: s (TMz, the default) or p (TEz)")
     return p.parse_args()
 
 
@@ -63,7 +65,17 @@ def workload(args, lam):
         spec = fi.config_c2(lambda0=lam, labels=_labels_cache("c2"))
     if args.fdtd_steps:
         spec = spec.with_(steps=args.fdtd_steps)
+    if getattr(args, "pol", "s") == "p":
+        spec = spec.with_(polarization=fi.POL_P)
     return spec
+
+
+def _oracle_class(spec):
+    if getattr(spec, "polarization", 0):
+        from oracle.fdtd_tez import TEzOracle
+        return TEzOracle
+    from oracle import TMzOracle
+    return TMzOracle
 
 
 _LABELS = {}
@@ -83,6 +95,7 @@ def describe(spec, args):
              "c3": "config 3 monocot cross-section with hyphae"}
     return {
         "workload": f"{names[args.config]} {spec.nx}x{spec.ny} cells, dx={spec.dx * 1e9:.0f} nm, "
+                    f"{'P (TEz)' if getattr(spec, 'polarization', 0) else 'S (TMz)'} polarisation, "
                     f"S={spec.courant:.2f}, {spec.steps} leapfrog steps per run, "
                     f"wavelengths 450/550/662/800/1450 nm cycled",
         "nx": spec.nx, "ny": spec.ny, "fdtd_steps_per_run": spec.steps,
@@ -177,8 +190,7 @@ def _max_over_ranks(world, v):
 def oracle_rate(spec, budget_s=12.0, min_steps=2):
     """Times the oracle as it stands on a bounded number of leapfrog steps of
     the same grid; returns (Gcell-updates/s, steps, seconds)."""
-    from oracle import TMzOracle
-    sim = TMzOracle(spec)
+    sim = _oracle_class(spec)(spec)
     sim.step()                                   # first step outside the clock
     steps, t0 = 0, time.perf_counter()
     while steps < min_steps or time.perf_counter() - t0 < budget_s:
@@ -193,8 +205,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     spec = workload(args, WAVELENGTHS[1])
-    from oracle import TMzOracle
-    sim = TMzOracle(spec)
+    sim = _oracle_class(spec)(spec)
     sample_steps = 2 if args.config != "c1" else 200
     for _ in range(args.warmup):
         for _ in range(sample_steps):
@@ -451,7 +462,8 @@ def main():
     algo_bytes = BYTES_PER_CELL_UPDATE * spec0.nx * spec0.ny * steps_per_launch
     peak, peak_kind = peaks()
     achieved = algo_bytes / avg_launch_s / 1e9 if avg_launch_s > 0 else None
-    traffic = measured_traffic(spec0, steps_per_launch) if kern == 2 else None
+    # the stored DRAM traffic was captured on the S kernel
+    traffic = measured_traffic(spec0, steps_per_launch) if kern == 2 and args.pol == "s" else None
     for s in sims.values():
         s.close()
 

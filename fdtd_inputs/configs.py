@@ -33,6 +33,9 @@ SOURCE_PULSE = 0   # Gaussian-modulated sinusoid
 SOURCE_CW = 1      # raised-cosine-ramped sinusoid
 SOURCE_NONE = 2    # no incident wave (fields come from an initial state)
 
+POL_S = 0          # S polarisation: E along z (TMz)
+POL_P = 1          # P polarisation: H along z (TEz)
+
 
 @dataclasses.dataclass
 class RunSpec:
@@ -62,6 +65,7 @@ class RunSpec:
     source_kind: int = SOURCE_PULSE
     rel_bandwidth: float = 0.1
     t0_over_tau: float = 5.0
+    polarization: int = POL_S     # POL_S: TMz (Ez, Hx, Hy); POL_P: TEz (Hz, Ex, Ey)
 
     @property
     def courant(self) -> float:

@@ -1,5 +1,6 @@
 /*
- * libfdtd: 2D TMz FDTD of segmented leaf cross-sections on one GPU (sm_103a).
+ * libfdtd: 2D FDTD (S: TMz, P: TEz) of segmented leaf cross-sections on one
+ * GPU (sm_103a).
  *
  * Problem statement (arXiv 2512.17132, Sec. 2.1 and Sec. 2.6): given a 2D
  * segmented cross-section (a label map), the grid step h and time step dt,
@@ -24,10 +25,21 @@
  *   - Running DFTs at w0 of Ez (rows r_row, t_row) and of the row-averaged
  *     Hx (Sec. 2.6) give Poynting fluxes; R and T are normalised by the same
  *     run on an empty (all-air) domain, which the library runs alongside.
+ *   - P polarisation (fdtd_source.polarization = FDTD_POL_P) runs the TEz
+ *     leapfrog of Sec. 2.3 instead: Hz at cell centres (times n+1/2), Ex on
+ *     the top and Ey on the left edge of each cell (times n); each step
+ *     updates Hz, then Ex and Ey. The loss coefficients C_e, C_h act on the
+ *     E components, so they live on the edges; an edge takes the mean eps_r
+ *     and sigma of the two cells it separates. The TF/SF line, CPML, monitors
+ *     (DFT of Hz and of the row-averaged Ex) and the empty-domain run follow
+ *     the S case with E and H exchanged.
  *
  * Storage on the device is FP32 with H kept as eta0*H; every field exchanged
  * through this interface is in SI units (V/m and A/m), FP32, dense row-major
- * (ny rows of nx values, x fastest), and may be host or device memory.
+ * (ny rows of nx values, x fastest), and may be host or device memory. The
+ * three field arrays of a handle are (Ez, Hx, Hy) for S polarisation and
+ * (Hz, Ex, Ey) for P polarisation: the centre field, the top-edge field and
+ * the left-edge field.
  *
  * All functions return FDTD_OK (0) or a negative FDTD_E* code; the message
  * of the last failure on a handle is fdtd_last_error(handle), and failures
@@ -85,9 +97,13 @@ typedef struct fdtd_material {
  * kind 2: no incident wave (fields come from fdtd_set_fields/load_state).
  * w0 = 2 pi c0 / lambda0 is also the DFT frequency and the frequency at
  * which sigma is evaluated. */
+#define FDTD_POL_S 0  /* TMz: Ez, Hx, Hy */
+#define FDTD_POL_P 1  /* TEz: Hz, Ex, Ey (at most 16 labels; labels, not maps) */
+
 typedef struct fdtd_source {
     int32_t kind;
-    int32_t reserved;        /* must be 0 */
+    int32_t polarization;    /* FDTD_POL_S or FDTD_POL_P (Sec. 2.1: the two runs
+                                of unpolarised light) */
     double lambda0;          /* [m] */
     double rel_bandwidth;
     double t0_over_tau;
@@ -168,12 +184,14 @@ int fdtd_flux_raw(fdtd_handle* h, double out[3]);
 /* Running DFT accumulators (Sec. 2.6) in SI units: 4 rows of nx complex
  * values, each stored as (re, im) doubles (8*nx doubles in total, host or
  * device), in the order Ez(r_row), Hx(r_row), Ez(t_row), Hx(t_row); the Hx
- * rows average the edges row and row+1. */
+ * rows average the edges row and row+1. P polarisation: Hz(r_row),
+ * Ex(r_row), Hz(t_row), Ex(t_row), with the Ex rows averaged alike. */
 int fdtd_get_dft(fdtd_handle* h, double* out);
 
 /* Read or overwrite the fields (SI, FP32, ny*nx each, host or device; a NULL
- * pointer skips that field). Hx row 0 is the fixed top edge and reads 0;
- * fdtd_set_fields forces it to 0. Synchronous. */
+ * pointer skips that field): (Ez, Hx, Hy) for S polarisation, (Hz, Ex, Ey)
+ * for P polarisation. Row 0 of the top-edge field (Hx, or Ex) is the fixed
+ * top wall and reads 0; fdtd_set_fields forces it to 0. Synchronous. */
 int fdtd_get_fields(fdtd_handle* h, float* ez, float* hx, float* hy);
 int fdtd_set_fields(fdtd_handle* h, const float* ez, const float* hx,
                     const float* hy);
@@ -211,7 +229,8 @@ void fdtd_destroy(fdtd_handle* h);
  * and the transpose of every update is applied in reverse order; per-segment
  * FP32 sums are accumulated in FP64. The handle keeps its final forward
  * state. FDTD_ESTATE if no checkpointed run precedes or no incident power
- * reached t_row. Synchronises. */
+ * reached t_row; FDTD_EINVAL for P-polarised handles (the adjoint covers
+ * the S case). Synchronises. */
 int fdtd_forward_checkpointed(fdtd_handle* h, int64_t steps, int32_t every);
 int fdtd_backward(fdtd_handle* h, double wR, double wT, double* g_eps, double* g_sigma,
                   double* g_label, double out[3]);
@@ -228,7 +247,8 @@ int fdtd_autotune(fdtd_handle* h, int32_t trial_launches);
  * per wavelength, polarisation and slice, Sec. 2.2 and Sec. 4; here they
  * share the GPU). A batch groups existing handles (same device, nx % 4 == 0
  * each; the handles must outlive the batch). fdtd_batch_run advances every
- * handle by `steps` in lockstep: one blocked-kernel launch per K steps
+ * handle by `steps` in lockstep (all handles of one batch share one
+ * polarisation, else FDTD_EINVAL): one blocked-kernel launch per K steps
  * covers the warp tasks of all simulations, the empty-domain runs go as one
  * launch on a side stream, and full chunks of launches are captured once
  * into a CUDA graph and replayed (FDTD_OPT_GRAPH). The results are exactly

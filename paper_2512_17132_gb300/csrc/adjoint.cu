@@ -188,7 +188,7 @@ __global__ void k_adj_e(AdjArgs a, int64_t n, const float* __restrict__ lE_in,
     }
     a.gA[o] = __fmaf_rn(eb, a.tE[o], a.gA[o]);
     a.gB[o] = __fmaf_rn(eb, curl, a.gB[o]);
-    float c0, g0, cl, gl, gu = 0.f, dummy;
+    float c0, g0, cl, gu = 0.f, dummy;
     adj_curl(a, j, i, lE_in, mE_in, mE_out, &c0, &g0);
     adj_curl(a, j, il, lE_in, mE_in, nullptr, &cl, &dummy);
     if (j > 0) adj_curl(a, j - 1, i, lE_in, mE_in, nullptr, &dummy, &gu);
@@ -334,6 +334,10 @@ int fdtd_forward_checkpointed(fdtd_handle* h, int64_t steps, int32_t every) {
     try {
         if (steps < 1 || every < 1) {
             h->err = "fdtd_forward_checkpointed: need steps >= 1 and every >= 1";
+            return FDTD_EINVAL;
+        }
+        if (h->src.polarization != FDTD_POL_S) {
+            h->err = "fdtd_forward_checkpointed: the adjoint covers S (TMz) handles only";
             return FDTD_EINVAL;
         }
         ACK(cudaSetDevice(h->device));

@@ -75,7 +75,7 @@ StepArgs step_args(fdtd_handle* h) {
     StepArgs a{};
     a.nx = h->g.nx; a.ny = h->g.ny; a.pitch = h->pitch; a.lpitch = h->lpitch;
     a.P = h->g.pml_cells; a.js = h->g.tfsf_row; a.jr = h->g.r_row; a.jt = h->g.t_row;
-    a.n_labels = h->n_labels; a.S = (float)h->S;
+    a.n_labels = h->n_labels; a.pol = h->src.polarization; a.S = (float)h->S;
     a.labels = h->labels; a.coef = h->coef; a.cellcoef = h->cellcoef;
     a.pml_e = h->pml_e; a.pml_h = h->pml_h;
     a.hinc = h->d_hinc; a.einc = h->d_einc; a.phE = h->d_phE; a.phH = h->d_phH;
@@ -199,7 +199,7 @@ BlockPlan& get_plan(fdtd_handle* h, int K) {
     const int min_seg = P + K + 1;
     int seg = want_seg;
     if (seg <= 0) {
-        int per_sm = blocked_warps_per_sm(K, h->opt_variant);
+        int per_sm = blocked_warps_per_sm(K, h->opt_variant, h->src.polarization);
         if (per_sm <= 0) per_sm = 8;
         const int64_t W = (int64_t)sm_count(h) * per_sm;
         double best = 1e300;
@@ -451,22 +451,41 @@ static int create_impl(const fdtd_grid* grid, const uint8_t* labels, const fdtd_
                     g.pml_alpha_max >= 0,
                 "grid: CPML parameters out of range");
         REQUIRE(n_labels >= 1 && n_labels <= 256, "table: need 1..256 labels");
-        REQUIRE(source->kind >= 0 && source->kind <= 2 && source->reserved == 0,
-                "source: kind must be 0, 1 or 2");
+        REQUIRE(source->kind >= 0 && source->kind <= 2, "source: kind must be 0, 1 or 2");
+        REQUIRE(source->polarization == FDTD_POL_S || source->polarization == FDTD_POL_P,
+                "source: polarization must be FDTD_POL_S (0) or FDTD_POL_P (1)");
+        const bool pol_p = source->polarization == FDTD_POL_P;
+        REQUIRE(!pol_p || (!maps && n_labels <= 16),
+                "source: P polarisation needs a label map with at most 16 labels");
         REQUIRE(source->lambda0 > 0, "source: lambda0 must be positive");
         REQUIRE(source->kind != 0 || source->rel_bandwidth > 0,
                 "source: rel_bandwidth must be positive");
         h->omega = 2.0 * kPi * kC0 / source->lambda0;
 
-        std::vector<float2> coef(n_labels);
+        // S: (C_e, S C_h / eps_r) per label (Sec. 2.3). P: the same per label
+        // pair (la << 4 | lb) with eps_r and sigma the means of the two labels,
+        // the material of an edge between two cells.
+        std::vector<double> leps(n_labels), lsig(n_labels);
         for (int l = 0; l < n_labels; ++l) {
             const double n = table[l].n, k = table[l].k;
             REQUIRE(n > 0 && k >= 0 && n > k, "table: need n > k >= 0 for every label");
-            const double eps = n * n - k * k;
-            const double sig = 2.0 * h->omega * kEps0 * n * k;
+            leps[l] = n * n - k * k;
+            lsig[l] = 2.0 * h->omega * kEps0 * n * k;
+        }
+        auto lossy = [&](double eps, double sig) {
             const double beta = sig * g.dt / (2.0 * kEps0 * eps);
-            coef[l] = make_float2((float)((1.0 - beta) / (1.0 + beta)),
-                                  (float)(h->S / (eps * (1.0 + beta))));
+            return make_float2((float)((1.0 - beta) / (1.0 + beta)),
+                               (float)(h->S / (eps * (1.0 + beta))));
+        };
+        const int n_coef = pol_p ? 256 : n_labels;
+        std::vector<float2> coef(n_coef, make_float2(1.0f, (float)h->S));
+        for (int la = 0; la < n_labels; ++la) {
+            if (!pol_p) {
+                coef[la] = lossy(leps[la], lsig[la]);
+                continue;
+            }
+            for (int lb = 0; lb < n_labels; ++lb)
+                coef[(la << 4) | lb] = lossy(0.5 * (leps[la] + leps[lb]), 0.5 * (lsig[la] + lsig[lb]));
         }
 
         CK(cudaGetDevice(&h->device));
@@ -497,7 +516,7 @@ static int create_impl(const fdtd_grid* grid, const uint8_t* labels, const fdtd_
             CK(cudaMemcpy2DAsync(h->labels, h->lpitch, labels, g.nx, g.nx, g.ny, cudaMemcpyDefault,
                                  h->stream));
         dalloc(h, &h->coef, 256);
-        CK(cudaMemcpyAsync(h->coef, coef.data(), n_labels * sizeof(float2), cudaMemcpyHostToDevice,
+        CK(cudaMemcpyAsync(h->coef, coef.data(), n_coef * sizeof(float2), cudaMemcpyHostToDevice,
                            h->stream));
         dalloc(h, &h->dft, (size_t)4 * g.nx);
         dalloc(h, &h->tw_ez, g.ny);
@@ -744,8 +763,12 @@ int fdtd_get_dft(fdtd_handle* h, double* out) {
         const size_t cnt = (size_t)8 * h->g.nx;
         std::vector<double> tmp(cnt);
         CK(cudaMemcpy(tmp.data(), h->dft, cnt * sizeof(double), cudaMemcpyDeviceToHost));
-        for (int row = 1; row < 4; row += 2)
-            for (size_t i = 0; i < (size_t)2 * h->g.nx; ++i) tmp[(size_t)row * 2 * h->g.nx + i] /= kEta0;
+        // S: rows 1, 3 hold eta0 Hx. P: rows 0, 2 hold eta0 Hz, rows 1, 3 hold -Ex.
+        const bool pol_p = h->src.polarization == FDTD_POL_P;
+        for (int row = 0; row < 4; ++row) {
+            const double sc = pol_p ? ((row & 1) ? -1.0 : 1.0 / kEta0) : ((row & 1) ? 1.0 / kEta0 : 1.0);
+            for (size_t i = 0; i < (size_t)2 * h->g.nx; ++i) tmp[(size_t)row * 2 * h->g.nx + i] *= sc;
+        }
         CK(cudaMemcpy(out, tmp.data(), cnt * sizeof(double), cudaMemcpyDefault));
         return FDTD_OK;
     } catch (const Fail& f) {
@@ -762,7 +785,11 @@ int fdtd_get_fields(fdtd_handle* h, float* ez, float* hx, float* hy) {
         float* tmp = nullptr;
         float* dst[3] = {ez, hx, hy};
         const float* src[3] = {h->ez[h->cur], h->hx[h->cur], h->hy[h->cur]};
-        const float scale[3] = {1.0f, (float)(1.0 / kEta0), (float)(1.0 / kEta0)};
+        // stored (S) Ez, eta0 Hx, eta0 Hy or (P) eta0 Hz, -Ex, -Ey
+        const bool pol_p = h->src.polarization == FDTD_POL_P;
+        const float scale[3] = {pol_p ? (float)(1.0 / kEta0) : 1.0f,
+                                pol_p ? -1.0f : (float)(1.0 / kEta0),
+                                pol_p ? -1.0f : (float)(1.0 / kEta0)};
         for (int f = 0; f < 3; ++f) {
             if (!dst[f]) continue;
             if (is_device_ptr(dst[f])) {
@@ -792,7 +819,9 @@ int fdtd_set_fields(fdtd_handle* h, const float* ez, const float* hx, const floa
         float* tmp = nullptr;
         const float* srcs[3] = {ez, hx, hy};
         float* dsts[3] = {h->ez[h->cur], h->hx[h->cur], h->hy[h->cur]};
-        const float scale[3] = {1.0f, (float)kEta0, (float)kEta0};
+        const bool pol_p = h->src.polarization == FDTD_POL_P;
+        const float scale[3] = {pol_p ? (float)kEta0 : 1.0f, pol_p ? -1.0f : (float)kEta0,
+                                pol_p ? -1.0f : (float)kEta0};
         for (int f = 0; f < 3; ++f) {
             if (!srcs[f]) continue;
             const float* s = srcs[f];

@@ -103,7 +103,7 @@ void drop_plan(fdtd_batch* b) {
 
 // Wave model over the union of the batch: waves x (rows + 2K).
 int model_seg(fdtd_batch* b, int K, int variant) {
-    int per_sm = blocked_warps_per_sm(K, variant);
+    int per_sm = blocked_warps_per_sm(K, variant, b->hs[0]->src.polarization);
     if (per_sm <= 0) per_sm = 8;
     const int64_t W = (int64_t)sm_count(b->hs[0]) * per_sm;
     const int w_int = 128 - 2 * ((K + 3) / 4 * 4);
@@ -237,13 +237,14 @@ int launches_per_chunk(int K) { return 2 * std::max(1, 512 / K); }
 // and the empty-domain columns on the side stream.
 void enqueue_chunk(fdtd_batch* b, int nl, int rem, int chunk_steps) {
     const BatchArgs a = batch_args(b);
+    const int pol = b->hs[0]->src.polarization;
     BCK(cudaEventRecord(b->ev_fork, b->stream));
     BCK(cudaStreamWaitEvent(b->side, b->ev_fork, 0));
     launch_twin_batch(b->d_twin, (int)b->hs.size(), b->max_ny, b->max_P, b->d_step_base,
                       chunk_steps, b->side);
     for (int j = 0; j < nl; ++j)
-        launch_blocked_batch(a, b->pK, b->pvar, j * b->pK, j & 1, b->stream);
-    if (rem > 0) launch_blocked_batch(a, rem, b->pvar, nl * b->pK, nl & 1, b->stream);
+        launch_blocked_batch(a, b->pK, b->pvar, j * b->pK, j & 1, pol, b->stream);
+    if (rem > 0) launch_blocked_batch(a, rem, b->pvar, nl * b->pK, nl & 1, pol, b->stream);
     BCK(cudaEventRecord(b->ev_join, b->side));
     BCK(cudaStreamWaitEvent(b->stream, b->ev_join, 0));
 }
@@ -274,12 +275,13 @@ double time_trial(fdtd_batch* b, int K, int variant, int seg, int trials) {
     upload_args(b, true);
     BCK(cudaMemsetAsync(b->d_step_base, 0, sizeof(int64_t), b->stream));
     const BatchArgs a = batch_args(b);
+    const int pol = b->hs[0]->src.polarization;
     cudaEvent_t e0, e1;
     BCK(cudaEventCreate(&e0));
     BCK(cudaEventCreate(&e1));
-    launch_blocked_batch(a, K, variant, 0, 0, b->stream);            // warm-up
+    launch_blocked_batch(a, K, variant, 0, 0, pol, b->stream);            // warm-up
     BCK(cudaEventRecord(e0, b->stream));
-    for (int t = 0; t < trials; ++t) launch_blocked_batch(a, K, variant, 0, 0, b->stream);
+    for (int t = 0; t < trials; ++t) launch_blocked_batch(a, K, variant, 0, 0, pol, b->stream);
     BCK(cudaEventRecord(e1, b->stream));
     BCK(cudaEventSynchronize(e1));
     float ms = 0.f;
@@ -350,6 +352,10 @@ int fdtd_batch_create(fdtd_handle* const* hs, int32_t n, fdtd_batch** out) {
             }
             if (hs[i]->device != hs[0]->device) {
                 b->err = "fdtd_batch_create: handles on different devices";
+                throw Fail{FDTD_EINVAL};
+            }
+            if (hs[i]->src.polarization != hs[0]->src.polarization) {
+                b->err = "fdtd_batch_create: all handles of a batch need one polarisation";
                 throw Fail{FDTD_EINVAL};
             }
             b->hs.push_back(hs[i]);
@@ -570,12 +576,14 @@ void fdtd_batch_destroy(fdtd_batch* b) {
 }
 
 // Single-handle autotuning: a batch of one, with its choice stored on the
-// handle and remembered per (nx, ny, pml_cells, device) for later handles.
+// handle and remembered per (nx, ny, pml_cells, polarisation, device) for
+// later handles.
 int fdtd_autotune(fdtd_handle* h, int32_t trial_launches) {
     if (!h) return FDTD_EINVAL;
     static std::mutex mu;
-    static std::map<std::tuple<int, int, int, int>, std::tuple<int, int, int>> cache;
-    const auto key = std::make_tuple(h->g.nx, h->g.ny, h->g.pml_cells, h->device);
+    static std::map<std::tuple<int, int, int, int, int>, std::tuple<int, int, int>> cache;
+    const auto key = std::make_tuple(h->g.nx, h->g.ny, h->g.pml_cells, h->src.polarization,
+                                     h->device);
     {
         std::lock_guard<std::mutex> lk(mu);
         auto it = cache.find(key);

@@ -16,6 +16,13 @@
 // Columns wrap modulo nx (periodic x, Sec. 2.4); the neighbour column of
 // the lane's outer column comes from the adjacent lane by shuffle.
 //
+// P polarisation (POL = 1, TEz in the variables eta0 Hz, -Ex, -Ey) runs the
+// same pipeline with loss-free centre updates and lossy edge updates whose
+// coefficients come from the label pair of each edge: the top edge of row r
+// pairs rows r-1 and r (level k+1 still holds the label word of row r-1 as
+// its pending row; level K keeps one extra word), the left edge of column q
+// pairs columns q-1 and q (the neighbour lane's last label by shuffle).
+//
 // CPML rows (top/bottom P rows) carry their psi recursion from level to
 // level in a per-strip scratch area; the segment plan guarantees that only
 // the first and last segment of a strip ever touch CPML rows. The TF/SF
@@ -67,11 +74,12 @@ constexpr int kRing = 4;   // rows in flight per warp for code shape 2
 }  // namespace
 
 // Register state of one warp's pipeline: per level k the pending row
-// (Ez, Hx, Hy, 4 packed labels); level K keeps Ez and Hx of its last row.
+// (Ez, Hx, Hy, 4 packed labels); level K keeps Ez and Hx of its last row
+// (and, for POL = 1, its label word).
 template <int K>
 struct Pipe {
     float E[K + 1][4], X[K + 1][4], Y[K][4];
-    uint32_t L[K];
+    uint32_t L[K + 1];
 };
 
 struct Lane {
@@ -85,7 +93,7 @@ struct Lane {
 // GENERAL = false is the lean path for iterations whose K rows hold no
 // CPML, source, monitor or boundary row and lie inside the valid range;
 // both paths round identically.
-template <int K, bool GENERAL>
+template <int K, bool GENERAL, int POL>
 __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[4],
                                         float (&fY)[4], uint32_t& fL, const int t,
                                         const BlockedArgs& a, const Lane& ln, float* slotE,
@@ -96,6 +104,14 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
         const int r = t - k - 1;
         float oE[4], oX[4], oY[4];
         const uint32_t cL = p.L[k];
+        // P: packed label-pair indices (labels < 16) of the top and left edges
+        uint32_t xP = 0u, yP = 0u;
+        if (POL == 1) {
+            const uint32_t lUp = p.L[k + 1];                          // row r-1
+            const uint32_t lNb = __shfl_up_sync(FULL, cL, 1) >> 24;   // column q-1 of lane 0
+            xP = (lUp << 4) | cL;
+            yP = (((cL << 8) | lNb) << 4) | cL;
+        }
         bool active = true;
         if (GENERAL) {
             const int lo = (ln.y0 == 0) ? 0 : (ln.y0 - K + k);
@@ -116,7 +132,7 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
                 else ld4_rw(slotE + (size_t)pe * 128, psi);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const float2 cc = ln.coef[(cL >> (8 * q)) & 0xffu];
+                    const float2 cc = POL ? make_float2(1.0f, S) : ln.coef[(cL >> (8 * q)) & 0xffu];
                     const float dhy = __fsub_rn(q < 3 ? p.Y[k][q + 1] : yR, p.Y[k][q]);
                     float dhx = __fsub_rn(fX[q], p.X[k][q]);
                     if (tf) dhx = __fsub_rn(dhx, hinc);
@@ -131,7 +147,7 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
             } else {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const float2 cc = ln.coef[(cL >> (8 * q)) & 0xffu];
+                    const float2 cc = POL ? make_float2(1.0f, S) : ln.coef[(cL >> (8 * q)) & 0xffu];
                     const float dhy = __fsub_rn(q < 3 ? p.Y[k][q + 1] : yR, p.Y[k][q]);
                     float dhx = __fsub_rn(fX[q], p.X[k][q]);
                     if (tf) dhx = __fsub_rn(dhx, hinc);
@@ -152,7 +168,12 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
                         float d = __fsub_rn(oE[q], p.E[k + 1][q]);
                         if (tf) d = __fsub_rn(d, einc);
                         psi[q] = psi_new(b, c, psi[q], d);
-                        oX[q] = h_new_pml(p.X[k][q], S, d, ik, psi[q]);
+                        if (POL == 1) {
+                            const float2 cx = ln.coef[(xP >> (8 * q)) & 0xffu];
+                            oX[q] = e_edge_new_pml(cx.x, cx.y, p.X[k][q], d, ik, psi[q]);
+                        } else {
+                            oX[q] = h_new_pml(p.X[k][q], S, d, ik, psi[q]);
+                        }
                     }
                     if (k == K - 1) {
                         if (ln.own) st4(a.psiH_out + (size_t)ph * a.s.pitch + ln.gx, psi);
@@ -164,7 +185,12 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
                     for (int q = 0; q < 4; ++q) {
                         float d = __fsub_rn(oE[q], p.E[k + 1][q]);
                         if (tf) d = __fsub_rn(d, einc);
-                        oX[q] = h_new(p.X[k][q], S, d);
+                        if (POL == 1) {
+                            const float2 cx = ln.coef[(xP >> (8 * q)) & 0xffu];
+                            oX[q] = e_edge_new(cx.x, cx.y, p.X[k][q], d);
+                        } else {
+                            oX[q] = h_new(p.X[k][q], S, d);
+                        }
                     }
                 }
             } else {
@@ -173,8 +199,15 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
             }
             const float eL = __shfl_up_sync(FULL, oE[3], 1);
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                oY[q] = h_new(p.Y[k][q], S, __fsub_rn(oE[q], q > 0 ? oE[q - 1] : eL));
+            for (int q = 0; q < 4; ++q) {
+                const float dy = __fsub_rn(oE[q], q > 0 ? oE[q - 1] : eL);
+                if (POL == 1) {
+                    const float2 cy = ln.coef[(yP >> (8 * q)) & 0xffu];
+                    oY[q] = e_edge_new(cy.x, cy.y, p.Y[k][q], dy);
+                } else {
+                    oY[q] = h_new(p.Y[k][q], S, dy);
+                }
+            }
             if (GENERAL && ln.own) {
                 if (ln.own_r && r == a.s.jr) {
                     const double2 ph = a.s.phE[n];
@@ -213,6 +246,7 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
         }
         p.L[k] = fL;
         fL = cL;
+        if (POL == 1 && k == K - 1) p.L[K] = cL;
     }
 }
 
@@ -220,7 +254,7 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
 // Code shapes V: 0 one row per loop trip with a one-row register prefetch;
 // 1 two rows per loop trip on plain stretches; 2 level-0 rows streamed
 // through a shared-memory ring filled kRing rows ahead by cp.async.
-template <int K, int V>
+template <int K, int V, int POL>
 __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float2* s_coef,
                                              const int task, const int64_t n0) {
     constexpr int H = ((K + 3) / 4) * 4;
@@ -251,7 +285,7 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float2*
             p.E[k][q] = 0.f; p.X[k][q] = 0.f;
             if (k < K) p.Y[k][q] = 0.f;
         }
-        if (k < K) p.L[k] = 0u;
+        p.L[k] = 0u;
     }
 
     const int y0 = ln.y0, y1 = ln.y1, ny = ln.ny, P = ln.P;
@@ -308,8 +342,8 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float2*
             fY[0] = y4.x; fY[1] = y4.y; fY[2] = y4.z; fY[3] = y4.w;
             issue(t + kRing, slot);
             slot = (slot + 1 == kRing) ? 0 : slot + 1;
-            if (is_fast(t)) advance<K, false>(p, fE, fX, fY, fL, t, a, ln, slotE, slotH, n0);
-            else advance<K, true>(p, fE, fX, fY, fL, t, a, ln, slotE, slotH, n0);
+            if (is_fast(t)) advance<K, false, POL>(p, fE, fX, fY, fL, t, a, ln, slotE, slotH, n0);
+            else advance<K, true, POL>(p, fE, fX, fY, fL, t, a, ln, slotE, slotH, n0);
             finish(t, fE, fX, fY);
         }
         cp_async_wait<0>();
@@ -342,8 +376,8 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float2*
             for (int q = 0; q < 4; ++q) { nE[q] = 0.f; nX[q] = 0.f; nY[q] = 0.f; }
             nL = 0u;
         }
-        if (fast) advance<K, false>(p, fE, fX, fY, fL, t, a, ln, slotE, slotH, n0);
-        else advance<K, true>(p, fE, fX, fY, fL, t, a, ln, slotE, slotH, n0);
+        if (fast) advance<K, false, POL>(p, fE, fX, fY, fL, t, a, ln, slotE, slotH, n0);
+        else advance<K, true, POL>(p, fE, fX, fY, fL, t, a, ln, slotE, slotH, n0);
         finish(t, fE, fX, fY);
     };
     int t = t_begin;
@@ -361,13 +395,14 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float2*
     }
 }
 
-template <int K, int V>
+template <int K, int V, int POL>
 __global__ void __launch_bounds__(32) k_blocked(const BlockedArgs a, const int64_t n0) {
     __shared__ float2 s_coef[256];
-    for (int t = threadIdx.x; t < a.s.n_labels; t += blockDim.x) s_coef[t] = a.s.coef[t];
+    const int n_coef = POL ? 256 : a.s.n_labels;
+    for (int t = threadIdx.x; t < n_coef; t += blockDim.x) s_coef[t] = a.s.coef[t];
     __syncwarp();
     if ((int)blockIdx.x >= a.n_tasks) return;       // one warp per block and task
-    blocked_task<K, V>(a, s_coef, blockIdx.x, n0);
+    blocked_task<K, V, POL>(a, s_coef, blockIdx.x, n0);
 }
 
 // Many independent simulations in one launch: the grid covers the union of
@@ -376,7 +411,7 @@ __global__ void __launch_bounds__(32) k_blocked(const BlockedArgs a, const int64
 // and runs the same task body. The absolute step of the launch is
 // n_base(sim) + *step_base + step_off, so a captured chunk of launches can be
 // replayed with a new *step_base.
-template <int K, int V>
+template <int K, int V, int POL>
 __global__ void __launch_bounds__(32) k_blocked_batch(const BatchArgs b, const int step_off,
                                                       const int parity) {
     __shared__ float2 s_coef[256];
@@ -390,16 +425,17 @@ __global__ void __launch_bounds__(32) k_blocked_batch(const BatchArgs b, const i
     for (int q = threadIdx.x; q < (int)(sizeof(BlockedArgs) / sizeof(int)); q += 32) d[q] = w[q];
     __syncwarp();
     const BlockedArgs& a = *reinterpret_cast<const BlockedArgs*>(s_raw);
-    for (int t = threadIdx.x; t < a.s.n_labels; t += 32) s_coef[t] = a.s.coef[t];
+    const int n_coef = POL ? 256 : a.s.n_labels;
+    for (int t = threadIdx.x; t < n_coef; t += 32) s_coef[t] = a.s.coef[t];
     __syncwarp();
     const int64_t n0 = a.n_base + *b.step_base + step_off;
-    blocked_task<K, V>(a, s_coef, task - b.first_task[sim], n0);
+    blocked_task<K, V, POL>(a, s_coef, task - b.first_task[sim], n0);
 }
 
-template <int K, int V>
+template <int K, int V, int POL>
 static int occupancy_warps() {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_blocked<K, V>, 32, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_blocked<K, V, POL>, 32, 0) != cudaSuccess)
         return 0;
     return b;
 }
@@ -408,12 +444,14 @@ int blocked_max_K() { return 8; }
 
 #define FDTD_BLOCKED_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8)
 
-int blocked_warps_per_sm(int K, int variant) {
+// P polarisation is built for code shape 2 only; other shapes map to it.
+int blocked_warps_per_sm(int K, int variant, int pol) {
     switch (K) {
-#define X(k)                                                               \
-    case k:                                                                \
-        return variant == 2 ? occupancy_warps<k, 2>()                      \
-                            : (variant ? occupancy_warps<k, 1>() : occupancy_warps<k, 0>());
+#define X(k)                                                                  \
+    case k:                                                                   \
+        if (pol) return occupancy_warps<k, 2, 1>();                           \
+        return variant == 2 ? occupancy_warps<k, 2, 0>()                      \
+                            : (variant ? occupancy_warps<k, 1, 0>() : occupancy_warps<k, 0, 0>());
         FDTD_BLOCKED_CASES(X)
 #undef X
         default: return 0;
@@ -421,14 +459,15 @@ int blocked_warps_per_sm(int K, int variant) {
 }
 
 bool launch_blocked_batch(const BatchArgs& b, int K, int variant, int step_off, int parity,
-                          cudaStream_t st) {
+                          int pol, cudaStream_t st) {
     const unsigned grid = (unsigned)b.n_tasks;
     switch (K) {
-#define X(k)                                                                            \
-    case k:                                                                             \
-        if (variant == 2) k_blocked_batch<k, 2><<<grid, 32, 0, st>>>(b, step_off, parity); \
-        else if (variant) k_blocked_batch<k, 1><<<grid, 32, 0, st>>>(b, step_off, parity); \
-        else k_blocked_batch<k, 0><<<grid, 32, 0, st>>>(b, step_off, parity);            \
+#define X(k)                                                                                   \
+    case k:                                                                                    \
+        if (pol) k_blocked_batch<k, 2, 1><<<grid, 32, 0, st>>>(b, step_off, parity);           \
+        else if (variant == 2) k_blocked_batch<k, 2, 0><<<grid, 32, 0, st>>>(b, step_off, parity); \
+        else if (variant) k_blocked_batch<k, 1, 0><<<grid, 32, 0, st>>>(b, step_off, parity);  \
+        else k_blocked_batch<k, 0, 0><<<grid, 32, 0, st>>>(b, step_off, parity);               \
         break;
         FDTD_BLOCKED_CASES(X)
 #undef X
@@ -442,9 +481,10 @@ bool launch_blocked(const BlockedArgs& a, int K, int variant, int64_t n0, cudaSt
     switch (K) {
 #define X(k)                                                                  \
     case k:                                                                   \
-        if (variant == 2) k_blocked<k, 2><<<grid, 32, 0, st>>>(a, n0);        \
-        else if (variant) k_blocked<k, 1><<<grid, 32, 0, st>>>(a, n0);        \
-        else k_blocked<k, 0><<<grid, 32, 0, st>>>(a, n0);                     \
+        if (a.s.pol) k_blocked<k, 2, 1><<<grid, 32, 0, st>>>(a, n0);          \
+        else if (variant == 2) k_blocked<k, 2, 0><<<grid, 32, 0, st>>>(a, n0); \
+        else if (variant) k_blocked<k, 1, 0><<<grid, 32, 0, st>>>(a, n0);     \
+        else k_blocked<k, 0, 0><<<grid, 32, 0, st>>>(a, n0);                  \
         break;
         FDTD_BLOCKED_CASES(X)
 #undef X

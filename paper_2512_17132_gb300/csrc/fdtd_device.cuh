@@ -10,6 +10,16 @@
 // with ca = (1-b)/(1+b), cb = S/(eps_r (1+b)), b = sigma dt/(2 eps0 eps_r).
 // In CPML rows the s-derivative d is replaced by d/kappa + psi with
 // psi <- b_pml psi + c_pml d (Roden-Gedney recursive convolution).
+//
+// P polarisation (TEz) runs on the same three buffers with the variables
+// F = eta0 Hz (centre), X = -Ex (top edge), Y = -Ey (left edge). In them the
+// TEz updates of Sec. 2.3 take the TMz form with the loss coefficients moved
+// from the centre to the edges:
+//   F <- F + S [ (Y[i+1]-Y[i]) + (X[j+1]-X[j]) ]
+//   X <- ce X + cb (F[j] - F[j-1]),   Y <- ce Y + cb (F[i] - F[i-1])
+// where (ce, cb) of an edge come from the mean eps_r and sigma of the two
+// cells it separates, and the incident pair, CPML, DFT and flux are those of
+// the TMz run (the TMz/TEz duality of the air lattice).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -37,6 +47,20 @@ __device__ __forceinline__ float h_new_pml(float h, float S, float d, float ik, 
     return __fmaf_rn(S, __fmaf_rn(d, ik, psi), h);
 }
 
+// Lossy edge update of P polarisation: ce X + cb d, and its CPML form.
+__device__ __forceinline__ float e_edge_new(float ce, float cb, float x, float d) {
+    return __fmaf_rn(cb, d, __fmul_rn(ce, x));
+}
+
+__device__ __forceinline__ float e_edge_new_pml(float ce, float cb, float x, float d, float ik,
+                                                float psi) {
+    return __fmaf_rn(cb, __fmaf_rn(d, ik, psi), __fmul_rn(ce, x));
+}
+
+// Index of the edge coefficient pair of two labels (< 16 each) in the
+// 256-entry table of a P-polarised handle.
+__device__ __forceinline__ int pair_index(unsigned la, unsigned lb) { return (int)((la << 4) | lb); }
+
 // Row-averaged Hx at a monitor row: edges row and row+1.
 __device__ __forceinline__ float hx_avg(float a, float b) {
     return __fmul_rn(0.5f, __fadd_rn(a, b));
@@ -57,9 +81,10 @@ struct StepArgs {
     int P;                // CPML rows per side
     int js, jr, jt;       // TF/SF row, monitor rows
     int n_labels;
+    int pol;              // 0: S (TMz), 1: P (TEz)
     float S;              // Courant number c0 dt / dx
     const uint8_t* labels;
-    const float2* coef;   // (ca, cb) per label
+    const float2* coef;   // S: (ca, cb) per label; P: (ce, cb) per label pair (pair_index)
     const float2* cellcoef;  // (ca, cb) per cell (pitch floats2 per row) or null
     const float* pml_e;   // [3][2P]: b, c, 1/kappa for Ez rows (top 0..P-1, then bottom)
     const float* pml_h;   // [3][2P]: same for Hx rows

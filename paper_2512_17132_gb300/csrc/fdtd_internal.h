@@ -91,12 +91,12 @@ void launch_check_finite(const float* p, int pitch, int nx, int ny, int* flag,
                          cudaStream_t st);
 bool launch_blocked(const BlockedArgs& a, int K, int variant, int64_t n0, cudaStream_t st);
 bool launch_blocked_batch(const BatchArgs& b, int K, int variant, int step_off, int parity,
-                          cudaStream_t st);
+                          int pol, cudaStream_t st);
 void configure_twin_batch();
 void launch_twin_batch(const TwinArgs* tws, int n, int max_ny, int max_P,
                        const int64_t* step_base, int steps, cudaStream_t st);
 int blocked_max_K();
-int blocked_warps_per_sm(int K, int variant);
+int blocked_warps_per_sm(int K, int variant, int pol = 0);
 
 // host helpers shared by the handle, batch and tuning code (api.cu); they
 // throw Fail with the handle's error message set

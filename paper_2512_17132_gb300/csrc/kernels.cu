@@ -6,8 +6,10 @@
 
 namespace fdtd {
 
-// Ez^{n-1/2} -> Ez^{n+1/2} on every cell (Sec. 2.3, TMz Ez update), with the
+// Centre field n-1/2 -> n+1/2 on every cell: Ez (S, Sec. 2.3 TMz Ez update)
+// or F = eta0 Hz (P, TEz Hz update, loss-free coefficients (1, S)), with the
 // CPML recursion in the top/bottom rows and the TF/SF correction at js.
+template <int POL>
 __global__ void k_naive_e(StepArgs a, float* __restrict__ ez, const float* __restrict__ hx,
                           const float* __restrict__ hy, float* __restrict__ psiE, int64_t n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -19,7 +21,9 @@ __global__ void k_naive_e(StepArgs a, float* __restrict__ ez, const float* __res
     const float hxb = (j + 1 < a.ny) ? hx[o + a.pitch] : 0.0f;         // Hx[ny] = 0
     float dhx = __fsub_rn(hxb, hx[o]);
     if (j == a.js) dhx = __fsub_rn(dhx, a.hinc[n]);                    // TF cell sees total Hx
-    const float2 c = a.cellcoef ? a.cellcoef[o] : a.coef[a.labels[(size_t)j * a.lpitch + i]];
+    float2 c;
+    if (POL == 0) c = a.cellcoef ? a.cellcoef[o] : a.coef[a.labels[(size_t)j * a.lpitch + i]];
+    else c = make_float2(1.0f, a.S);
     const float e = ez[o];
     const int pj = pml_e_index(j, a.ny, a.P);
     if (pj >= 0) {
@@ -33,7 +37,10 @@ __global__ void k_naive_e(StepArgs a, float* __restrict__ ez, const float* __res
     }
 }
 
-// H^n -> H^{n+1} (Sec. 2.3, TMz Hx and Hy updates). Hx row 0 stays 0.
+// Edge fields n -> n+1: Hx, Hy (S, TMz updates, coefficient S) or X = -Ex,
+// Y = -Ey (P, TEz updates, lossy coefficients of each edge's label pair).
+// Row 0 of the top-edge field stays 0.
+template <int POL>
 __global__ void k_naive_h(StepArgs a, const float* __restrict__ ez, float* __restrict__ hx,
                           float* __restrict__ hy, float* __restrict__ psiH, int64_t n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -42,24 +49,34 @@ __global__ void k_naive_h(StepArgs a, const float* __restrict__ ez, float* __res
     const size_t o = (size_t)j * a.pitch + i;
     const int il = (i == 0) ? a.nx - 1 : i - 1;                        // periodic x
     const float e = ez[o];
-    hy[o] = h_new(hy[o], a.S, __fsub_rn(e, ez[(size_t)j * a.pitch + il]));
+    const size_t lo = (size_t)j * a.lpitch;
+    if (POL == 0) {
+        hy[o] = h_new(hy[o], a.S, __fsub_rn(e, ez[(size_t)j * a.pitch + il]));
+    } else {
+        const float2 cy = a.coef[pair_index(a.labels[lo + il], a.labels[lo + i])];
+        hy[o] = e_edge_new(cy.x, cy.y, hy[o], __fsub_rn(e, ez[(size_t)j * a.pitch + il]));
+    }
     if (j > 0) {
         float d = __fsub_rn(e, ez[o - a.pitch]);
         if (j == a.js) d = __fsub_rn(d, a.einc[n]);                    // SF edge sees scattered Ez
+        float2 cx = make_float2(1.0f, a.S);
+        if (POL == 1) cx = a.coef[pair_index(a.labels[lo - a.lpitch + i], a.labels[lo + i])];
         const int pj = pml_h_index(j, a.ny, a.P);
         if (pj >= 0) {
             const float b = a.pml_h[pj], cc = a.pml_h[2 * a.P + pj], ik = a.pml_h[4 * a.P + pj];
             float* pp = psiH + (size_t)pj * a.pitch + i;
             const float p = psi_new(b, cc, *pp, d);
             *pp = p;
-            hx[o] = h_new_pml(hx[o], a.S, d, ik, p);
+            hx[o] = (POL == 0) ? h_new_pml(hx[o], a.S, d, ik, p)
+                               : e_edge_new_pml(cx.x, cx.y, hx[o], d, ik, p);
         } else {
-            hx[o] = h_new(hx[o], a.S, d);
+            hx[o] = (POL == 0) ? h_new(hx[o], a.S, d) : e_edge_new(cx.x, cx.y, hx[o], d);
         }
     }
 }
 
-// Running DFT of the monitor rows after step n (Sec. 2.6).
+// Running DFT of the monitor rows after step n (Sec. 2.6); in P polarisation
+// the same buffers hold eta0 Hz and -Ex.
 __global__ void k_naive_dft(StepArgs a, const float* __restrict__ ez,
                             const float* __restrict__ hx, int64_t n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -75,8 +92,13 @@ void launch_naive_step(const StepArgs& a, float* ez, float* hx, float* hy, float
                        float* psiH, int64_t n, cudaStream_t st) {
     dim3 blk(256);
     dim3 grd((a.nx + 255) / 256, a.ny);
-    k_naive_e<<<grd, blk, 0, st>>>(a, ez, hx, hy, psiE, n);
-    k_naive_h<<<grd, blk, 0, st>>>(a, ez, hx, hy, psiH, n);
+    if (a.pol == 0) {
+        k_naive_e<0><<<grd, blk, 0, st>>>(a, ez, hx, hy, psiE, n);
+        k_naive_h<0><<<grd, blk, 0, st>>>(a, ez, hx, hy, psiH, n);
+    } else {
+        k_naive_e<1><<<grd, blk, 0, st>>>(a, ez, hx, hy, psiE, n);
+        k_naive_h<1><<<grd, blk, 0, st>>>(a, ez, hx, hy, psiH, n);
+    }
     k_naive_dft<<<dim3((a.nx + 255) / 256, 2), blk, 0, st>>>(a, ez, hx, n);
 }
 

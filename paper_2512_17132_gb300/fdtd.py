@@ -16,6 +16,7 @@ FDTD_OK, FDTD_EINVAL, FDTD_ENOMEM, FDTD_ECUDA = 0, -1, -2, -3
 FDTD_EUNSTABLE, FDTD_ETIMEOUT, FDTD_ESTATE = -4, -5, -6
 FDTD_OPT_KERNEL, FDTD_OPT_BLOCK_STEPS, FDTD_OPT_SEG_ROWS = 1, 2, 3
 FDTD_OPT_TIMING, FDTD_OPT_WATCHDOG, FDTD_OPT_VARIANT, FDTD_OPT_GRAPH = 4, 5, 6, 7
+FDTD_POL_S, FDTD_POL_P = 0, 1
 KERNEL_AUTO, KERNEL_NAIVE, KERNEL_BLOCKED = 0, 1, 2
 
 
@@ -31,7 +32,7 @@ class fdtd_material(C.Structure):
 
 
 class fdtd_source(C.Structure):
-    _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("lambda0", C.c_double),
+    _fields_ = [("kind", C.c_int32), ("polarization", C.c_int32), ("lambda0", C.c_double),
                 ("rel_bandwidth", C.c_double), ("t0_over_tau", C.c_double)]
 
 
@@ -127,7 +128,9 @@ def make_grid(spec) -> fdtd_grid:
 
 
 def make_source(spec) -> fdtd_source:
-    return fdtd_source(int(spec.source_kind), 0, float(spec.lambda0),
+    """The source of a spec; spec.polarization (0 = S/TMz, 1 = P/TEz) defaults to S."""
+    return fdtd_source(int(spec.source_kind), int(getattr(spec, "polarization", FDTD_POL_S)),
+                       float(spec.lambda0),
                        float(spec.rel_bandwidth), float(spec.t0_over_tau))
 
 

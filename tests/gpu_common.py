@@ -41,16 +41,20 @@ class OracleTrace:
 
     def __init__(self, spec, snaps):
         from oracle import TMzOracle
-        self.sim = TMzOracle(spec)
+        from oracle.fdtd_tez import TEzOracle
+        pol = int(getattr(spec, "polarization", 0))
+        self.sim = TEzOracle(spec) if pol else TMzOracle(spec)
         self.snaps = {}
         self.max_norm = [0.0, 0.0]
         for n in range(1, max(snaps) + 1):
             self.sim.step()
-            e = float(np.linalg.norm(self.sim.ez))
-            h = math.hypot(np.linalg.norm(self.sim.hx), np.linalg.norm(self.sim.hy))
+            # centre field and the edge-field vector: (Ez; Hx, Hy) or (Hz; Ex, Ey)
+            c, x, y = self.sim.fields()
+            e = float(np.linalg.norm(c))
+            h = math.hypot(np.linalg.norm(x), np.linalg.norm(y))
             self.max_norm = [max(self.max_norm[0], e), max(self.max_norm[1], h)]
             if n in snaps:
-                self.snaps[n] = self.sim.fields()
+                self.snaps[n] = (c, x, y)
 
 
 def field_errors(gpu_fields, ref_fields, max_norms):
