@@ -206,6 +206,12 @@ class TEzOracle:
             self.step()
         return self
 
+    def reset_dft(self):
+        """Restart the running DFTs at the current step (a CW steady-state
+        window, Sec. 2.6: sampling starts once the fields are periodic)."""
+        for v in self.dft.values():
+            v[:] = 0.0
+
     def fields(self):
         return self.hz.copy(), self.ex.copy(), self.ey.copy()
 

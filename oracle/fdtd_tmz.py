@@ -257,6 +257,12 @@ class TMzOracle:
             self.step()
         return self
 
+    def reset_dft(self):
+        """Restart the running DFTs at the current step (a CW steady-state
+        window, Sec. 2.6: sampling starts once the fields are periodic)."""
+        for v in self.dft.values():
+            v[:] = 0.0
+
     # -- state access --------------------------------------------------------
     def fields(self):
         return self.ez.copy(), self.hx.copy(), self.hy.copy()
