@@ -41,7 +41,7 @@ def parse_args():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
+    p.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "campaign"])
     p.add_argument("--fdtd-steps", type=int, default=0,
                    help="leapfrog steps per run (default: the config's own count)")
     p.add_argument("--kernel", type=int, default=0)
@@ -340,6 +340,76 @@ def run_c4(args):
     return 0
 
 
+def run_campaign_bench(args):
+    """Spectrum/slice campaign (Sec. 4) on the config-2 cross-section: the
+    2000-column section cut into five 400-column slices, the five config-2
+    wavelengths, both polarisations (50 independent runs), slice- and
+    polarisation-averaged. One bench step = one whole campaign on resident
+    handles (one tuned batch per polarisation); e2e repeats it through
+    run_campaign from the host label map (handles created and destroyed)."""
+    import torch
+    import fdtd_inputs as fi
+    torch.cuda.set_device(0)
+    from paper_2512_17132_gb300 import build as b
+    b.build()
+    from paper_2512_17132_gb300 import fdtd
+    from paper_2512_17132_gb300.campaign import Campaign, run_campaign
+    steps = args.fdtd_steps or 30000
+    labels = _labels_cache("c2")
+
+    def make(lam):
+        return fi.config_c2(lambda0=lam, labels=labels, steps=steps)
+
+    wl = list(fi.C2_WAVELENGTHS)
+    camp = Campaign(make, wl, n_slices=5, timing=True)
+    cells = camp.cell_updates_per_step * steps
+    for _ in range(args.warmup):
+        camp.run(steps)
+    torch.cuda.synchronize()
+    before = camp.stats()
+    clocks = ClockSampler(_device_id())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        res = camp.run(steps)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    clk = clocks.stop()
+    after = camp.stats()
+    launches = sum(a["total_launches"] - b_["total_launches"] for a, b_ in zip(after, before))
+    camp.close()
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for _ in range(args.steps):
+            run_campaign(make, wl, n_slices=5, steps=steps)
+        torch.cuda.synchronize()
+        e_el = time.perf_counter() - t1
+        h2d = 2 * labels.nbytes + 50 * steps * (4 + 4 + 16 + 16)
+        e2e = {"value": args.steps * cells / e_el / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 50 * 3 * 8,
+               "ms_per_step": e_el / args.steps * 1e3,
+               "note": "per step: run_campaign from the host label map (50 handles created, "
+                       "batched, autotuned, run, flux read, destroyed)"}
+    line = {
+        "metric": METRIC, "value": args.steps * cells / el / 1e9, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"campaign: config-2 dicot 2000x12500 cut into 5 slices of 400 "
+                               f"columns x 5 wavelengths (450-1450 nm) x 2 polarisations, "
+                               f"{steps} leapfrog steps per run, averaged (Sec. 4)",
+                   "runs_per_step": len(camp.specs), "cell_updates_per_step": cells,
+                   "l2": "inputs larger than L2 (50 runs x 2 x 60 MB of fields)"},
+        "spectrum": {"lambda_nm": [round(x * 1e9) for x in wl], "R": list(map(float, res["R"])),
+                     "T": list(map(float, res["T"])), "A": list(map(float, res["A"]))},
+        "e2e": e2e, "clocks": clk, "gpu_launches": int(launches),
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def run_c5(args):
     """Config 5: gradient of R(550 nm) on the config-1 stack at 1000 x 6000
     cells, 30 000 steps, checkpoints every 500 steps: the checkpointed forward
@@ -401,6 +471,8 @@ def main():
         return run_c4(args)
     if args.config == "c5":
         return run_c5(args)
+    if args.config == "campaign":
+        return run_campaign_bench(args)
     world, rank, local = dist_setup(args)
     import torch
     if world > 1:

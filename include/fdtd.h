@@ -188,6 +188,38 @@ int fdtd_flux_raw(fdtd_handle* h, double out[3]);
  * Ex(r_row), Hz(t_row), Ex(t_row), with the Ex rows averaged alike. */
 int fdtd_get_dft(fdtd_handle* h, double* out);
 
+/* CW steady state (Sec. 2.6: the fields are sampled over whole periods once
+ * they are periodic): zero the running DFTs of the handle and of its
+ * empty-domain run, so that the next fdtd_run steps form the window. With a
+ * ramped CW source (kind 1), run past the ramp and the transient, call this,
+ * then run an integer number of periods (lambda0 / (c0 dt) steps each).
+ * Synchronous. */
+int fdtd_reset_dft(fdtd_handle* h);
+
+/* Bloch-order decomposition of the monitor lines (Sec. 2.6). The fields are
+ * periodic in x with period L = nx dx, so each DFT line expands as
+ * sum_m X_m exp(i 2 pi m x / L). For m = -m_max..m_max (2 m_max + 1 <= nx),
+ * out[8 (m + m_max) + q] (host memory, 8 (2 m_max + 1) doubles) holds:
+ *   q = 0, 1: order m's share of the Poynting fluxes, P_up,m / P_inc and
+ *             P_down,m / P_inc (Parseval: the shares of all nx orders sum to
+ *             R and T of fdtd_flux; evanescent orders carry none);
+ *   q = 2, 3: the paper's |E_ref,m|^2 / |E_inc,0|^2 and |E_trs,m|^2 /
+ *             |E_inc,0|^2 with E = Ez (S) or the row-averaged Ex (P) and
+ *             E_inc,0 from the empty-domain run;
+ *   q = 4, 5: the same times the obliquity factor w_m (the power an oblique
+ *             order carries per |E_m|^2 relative to order 0, which the
+ *             paper's sum leaves out);
+ *   q = 6:    w_m = sin(k_y,m dx)/sin(k_y,0 dx) for S, its inverse for P,
+ *             0 for evanescent orders;
+ *   q = 7:    k_y,m dx from the 2D lattice dispersion relation
+ *             sin^2(k_y dx/2) = sin^2(w0 dt/2)/S^2 - sin^2(pi m/nx), NaN when
+ *             the order is evanescent.
+ * The order amplitudes are computed on the device in FP64. Synchronous.
+ * fdtd_bloch_propagating returns the largest M such that every |m| <= M is
+ * a propagating order (and 2M + 1 <= nx), or FDTD_EINVAL for NULL. */
+int fdtd_bloch_orders(fdtd_handle* h, int32_t m_max, double* out);
+int32_t fdtd_bloch_propagating(const fdtd_handle* h);
+
 /* Read or overwrite the fields (SI, FP32, ny*nx each, host or device; a NULL
  * pointer skips that field): (Ez, Hx, Hy) for S polarisation, (Hz, Ex, Ey)
  * for P polarisation. Row 0 of the top-edge field (Hx, or Ex) is the fixed

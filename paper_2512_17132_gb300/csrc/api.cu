@@ -756,6 +756,98 @@ int fdtd_flux_raw(fdtd_handle* h, double out[3]) {
     }
 }
 
+int fdtd_reset_dft(fdtd_handle* h) {
+    if (!h) return FDTD_EINVAL;
+    try {
+        CK(cudaSetDevice(h->device));
+        sync_all(h);
+        CK(cudaMemsetAsync(h->dft, 0, (size_t)4 * h->g.nx * sizeof(double2), h->stream));
+        CK(cudaMemsetAsync(h->tw_dft, 0, 4 * sizeof(double2), h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        return FDTD_OK;
+    } catch (const Fail& f) {
+        return f.code;
+    }
+}
+
+namespace {
+
+// k_y dx of Bloch order m on the 2D lattice:
+// sin^2(k_y dx/2) = sin^2(w dt/2)/S^2 - sin^2(pi m/nx); NaN when evanescent.
+double bloch_ky(int64_t m, int nx, double S, double wdt) {
+    const double a = std::sin(0.5 * wdt) / S;
+    const double b = std::sin(kPi * (double)m / (double)nx);
+    const double s2 = a * a - b * b;
+    if (!(s2 > 0.0) || s2 > 1.0) return std::nan("");
+    return 2.0 * std::asin(std::sqrt(s2));
+}
+
+}  // namespace
+
+int32_t fdtd_bloch_propagating(const fdtd_handle* h) {
+    if (!h) return FDTD_EINVAL;
+    const double wdt = h->omega * h->g.dt;
+    int32_t M = 0;
+    while (2 * (M + 1) + 1 <= h->g.nx && std::isfinite(bloch_ky(M + 1, h->g.nx, h->S, wdt))) ++M;
+    return M;
+}
+
+int fdtd_bloch_orders(fdtd_handle* h, int32_t m_max, double* out) {
+    if (!h || !out) return FDTD_EINVAL;
+    double2* d_ord = nullptr;
+    try {
+        REQUIRE(m_max >= 0 && 2 * (int64_t)m_max + 1 <= h->g.nx,
+                "fdtd_bloch_orders: need 0 <= m_max and 2 m_max + 1 <= nx");
+        CK(cudaSetDevice(h->device));
+        sync_all(h);
+        const int n_ord = 2 * m_max + 1;
+        CK(cudaMalloc(&d_ord, (size_t)4 * n_ord * sizeof(double2)));
+        launch_bloch(h->dft, h->g.nx, m_max, d_ord, h->stream);
+        CK(cudaGetLastError());
+        h->total_launches += 1;
+        std::vector<double2> ord((size_t)4 * n_ord);
+        double2 tw[4];
+        CK(cudaMemcpyAsync(ord.data(), d_ord, ord.size() * sizeof(double2), cudaMemcpyDeviceToHost,
+                           h->stream));
+        CK(cudaMemcpyAsync(tw, h->tw_dft, sizeof(tw), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        cudaFree(d_ord);
+        d_ord = nullptr;
+        // Stored lines (both polarisations, in the device variables): 0 centre
+        // field at r_row, 1 averaged edge field at r_row, 2 and 3 at t_row.
+        // The flux identities are those of fdtd_flux; the paper's amplitude is
+        // the centre field (Ez) for S and the edge field (Ex) for P.
+        const bool pol_p = h->src.polarization == FDTD_POL_P;
+        const double nx = (double)h->g.nx;
+        const double inc = -(tw[2].x * tw[3].x + tw[2].y * tw[3].y) * nx;
+        const double2 e_inc = pol_p ? tw[3] : tw[2];
+        const double a_inc = e_inc.x * e_inc.x + e_inc.y * e_inc.y;
+        const double wdt = h->omega * h->g.dt;
+        const double ky0 = bloch_ky(0, h->g.nx, h->S, wdt);
+        for (int o = 0; o < n_ord; ++o) {
+            const double2 er = ord[o], hr = ord[n_ord + o];
+            const double2 et = ord[2 * n_ord + o], ht = ord[3 * n_ord + o];
+            const double2 ar = pol_p ? hr : er, at = pol_p ? ht : et;
+            const double ky = bloch_ky(o - m_max, h->g.nx, h->S, wdt);
+            double w = 0.0;
+            if (std::isfinite(ky)) w = pol_p ? std::sin(ky0) / std::sin(ky) : std::sin(ky) / std::sin(ky0);
+            double* r = out + (size_t)8 * o;
+            r[0] = nx * (er.x * hr.x + er.y * hr.y) / inc;
+            r[1] = -nx * (et.x * ht.x + et.y * ht.y) / inc;
+            r[2] = (ar.x * ar.x + ar.y * ar.y) / a_inc;
+            r[3] = (at.x * at.x + at.y * at.y) / a_inc;
+            r[4] = w * r[2];
+            r[5] = w * r[3];
+            r[6] = w;
+            r[7] = ky;
+        }
+        return FDTD_OK;
+    } catch (const Fail& f) {
+        if (d_ord) cudaFree(d_ord);
+        return f.code;
+    }
+}
+
 int fdtd_get_dft(fdtd_handle* h, double* out) {
     if (!h || !out) return FDTD_EINVAL;
     try {

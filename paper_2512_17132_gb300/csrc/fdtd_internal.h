@@ -87,6 +87,7 @@ void launch_pack(const float* src, int pitch, int nx, int ny, float scale, float
 void launch_unpack(const float* src, int nx, int ny, float scale, float* dst, int pitch,
                    cudaStream_t st);
 void launch_scale_double(double* p, int64_t n, double scale, cudaStream_t st);
+void launch_bloch(const double2* dft, int nx, int m_max, double2* out, cudaStream_t st);
 void launch_check_finite(const float* p, int pitch, int nx, int ny, int* flag,
                          cudaStream_t st);
 bool launch_blocked(const BlockedArgs& a, int K, int variant, int64_t n0, cudaStream_t st);

@@ -317,6 +317,52 @@ void launch_flux(const double2* dft, const double2* twin_dft, int nx, double* ou
     k_flux<<<1, 1024, 0, st>>>(dft, twin_dft, nx, out);
 }
 
+// Bloch-order amplitudes of the four monitor lines (Sec. 2.6): block o
+// computes, for m = o - m_max, X_m = (1/nx) sum_i X_i exp(-2 pi i m i / nx)
+// for each line X in FP64. The phase index m i is reduced modulo nx in
+// integers before sincospi, so the twiddles are exact to rounding.
+__global__ void __launch_bounds__(256) k_bloch(const double2* __restrict__ dft, int nx,
+                                               int m_max, double2* __restrict__ out) {
+    __shared__ double2 sh[4][8];
+    const int o = blockIdx.x;
+    const int64_t m = (int64_t)o - m_max;
+    const int64_t mm = ((m % nx) + nx) % nx;
+    double2 acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = make_double2(0.0, 0.0);
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        const int64_t r = (mm * i) % nx;
+        double sn, cs;
+        sincospi(2.0 * (double)r / (double)nx, &sn, &cs);      // e^{-i theta} = cs - i sn
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const double2 v = dft[(size_t)q * nx + i];
+            acc[q].x = fma(v.x, cs, fma(v.y, sn, acc[q].x));
+            acc[q].y = fma(v.y, cs, fma(-v.x, sn, acc[q].y));
+        }
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        for (int s = 16; s > 0; s >>= 1) {
+            acc[q].x += __shfl_down_sync(0xffffffffu, acc[q].x, s);
+            acc[q].y += __shfl_down_sync(0xffffffffu, acc[q].y, s);
+        }
+        if (l == 0) sh[q][w] = acc[q];
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        const int q = threadIdx.x;
+        double2 t = make_double2(0.0, 0.0);
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { t.x += sh[q][k].x; t.y += sh[q][k].y; }
+        out[(size_t)q * (2 * m_max + 1) + o] = make_double2(t.x / nx, t.y / nx);
+    }
+}
+
+void launch_bloch(const double2* dft, int nx, int m_max, double2* out, cudaStream_t st) {
+    k_bloch<<<2 * m_max + 1, 256, 0, st>>>(dft, nx, m_max, out);
+}
+
 __global__ void k_pack(const float* __restrict__ src, int pitch, int nx, int ny, float scale,
                        float* __restrict__ dst) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;

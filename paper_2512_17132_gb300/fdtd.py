@@ -71,6 +71,9 @@ def load_library(path: str = LIB_PATH):
         "fdtd_flux": (C.c_int, [vp, dp, dp]),
         "fdtd_flux_raw": (C.c_int, [vp, dp]),
         "fdtd_get_dft": (C.c_int, [vp, vp]),
+        "fdtd_reset_dft": (C.c_int, [vp]),
+        "fdtd_bloch_orders": (C.c_int, [vp, i32, vp]),
+        "fdtd_bloch_propagating": (i32, [vp]),
         "fdtd_get_fields": (C.c_int, [vp, vp, vp, vp]),
         "fdtd_set_fields": (C.c_int, [vp, vp, vp, vp]),
         "fdtd_state_bytes": (C.c_size_t, [vp]),
@@ -217,6 +220,29 @@ def fdtd_get_dft(h, nx: int):
     _check(load_library().fdtd_get_dft(h, _ptr(out)), h)
     z = out.reshape(4, nx, 2)
     return z[..., 0] + 1j * z[..., 1]
+
+
+def fdtd_reset_dft(h):
+    _check(load_library().fdtd_reset_dft(h), h)
+
+
+def fdtd_bloch_propagating(h) -> int:
+    r = int(load_library().fdtd_bloch_propagating(h))
+    _check(min(r, 0), h)
+    return r
+
+
+BLOCH_FIELDS = ("R_flux", "T_flux", "R_paper", "T_paper", "R_corr", "T_corr", "w", "ky")
+
+
+def fdtd_bloch_orders(h, m_max: int):
+    """Per-order quantities for m = -m_max..m_max as a dict of numpy arrays
+    (keys "m" and BLOCH_FIELDS, in the order of the C interface)."""
+    out = np.empty((max(2 * int(m_max) + 1, 1), 8), dtype=np.float64)
+    _check(load_library().fdtd_bloch_orders(h, int(m_max), _ptr(out)), h)
+    d = {k: out[:, q].copy() for q, k in enumerate(BLOCH_FIELDS)}
+    d["m"] = np.arange(-m_max, m_max + 1)
+    return d
 
 
 def fdtd_get_fields(h, ny: int, nx: int, out=None):
@@ -428,6 +454,16 @@ class Simulation:
 
     def dft(self):
         return fdtd_get_dft(self.h, self.spec.nx)
+
+    def reset_dft(self):
+        fdtd_reset_dft(self.h)
+        return self
+
+    def bloch(self, m_max=None):
+        """Bloch orders -m_max..m_max (default: every propagating order)."""
+        if m_max is None:
+            m_max = fdtd_bloch_propagating(self.h)
+        return fdtd_bloch_orders(self.h, m_max)
 
     def fields(self):
         return fdtd_get_fields(self.h, self.spec.ny, self.spec.nx)
