@@ -237,7 +237,7 @@ def run_reference(args):
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("blocked.cu", "fdtd_device.cuh"):
+    for f in ("blocked_impl.cuh", "blocked_s.cu", "fdtd_device.cuh"):
         with open(os.path.join(ROOT, "paper_2512_17132_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

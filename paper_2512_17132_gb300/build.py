@@ -17,7 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfdtd.so")
-SOURCES = ["api.cu", "kernels.cu", "blocked.cu", "batch.cu", "adjoint.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "kernels.cu", "blocked.cu", "blocked_s.cu", "blocked_sb.cu", "blocked_p.cu",
+           "batch.cu", "adjoint.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -642,9 +642,12 @@ int fdtd_run(fdtd_handle* h, int64_t steps) {
         tw.hinc = h->d_hinc; tw.einc = h->d_einc; tw.phE = h->d_phE; tw.phH = h->d_phH;
         tw.ez = h->tw_ez; tw.hx = h->tw_hx; tw.psiE = h->tw_psiE; tw.psiH = h->tw_psiH;
         tw.dft = h->tw_dft;
+        // chunks of whole blocked launches, so only the run's last launch is short
+        const int64_t kb = (kern == 2) ? std::max(1, std::min(h->opt_block, blocked_max_K())) : 1;
+        const int64_t chunk = std::max<int64_t>(kb, kChunk - kChunk % kb);
         int64_t s = h->n;
         while (s < n_end) {
-            const int64_t ce = std::min(n_end, s + kChunk);
+            const int64_t ce = std::min(n_end, s + chunk);
             produce_tables(h, std::max(ce, h->tab_uploaded));
             CK(cudaEventRecord(h->ev_tab, h->stream));
             CK(cudaStreamWaitEvent(h->twin_stream, h->ev_tab, 0));
@@ -1044,7 +1047,7 @@ int fdtd_set_option(fdtd_handle* h, int32_t option, int64_t value) {
             h->opt_watchdog = value;
             return FDTD_OK;
         case FDTD_OPT_VARIANT:
-            if (value < 0 || value > 2) break;
+            if (value < 0 || value > 3) break;
             h->opt_variant = (int)value;
             return FDTD_OK;
         default:

@@ -34,7 +34,7 @@ struct fdtd_batch {
     int device = 0;
     cudaStream_t stream = nullptr, side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_in = nullptr;
-    int K = 8, variant = 2, seg = 0, timing = 0, use_graph = 1;
+    int K = 7, variant = 3, seg = 0, timing = 0, use_graph = 1;
     // plan
     bool planned = false;
     int pK = 0, pvar = -1, pseg = -1, seg_used = 0;
@@ -310,8 +310,9 @@ int batch_tune(fdtd_batch* b, int trials) {
     double best = -1;
     int bK = b->K, bv = b->variant, bs = 0;
     for (int K : {8, 7, 6}) {
-        for (int v : {0, 1, 2}) {
+        for (int v : {0, 1, 2, 3}) {
             if (K == 8 && v == 1) continue;          // exceeds the register file at K = 8
+            if (b->hs[0]->src.polarization && v < 2) continue;   // P: shapes 2 and 3 only
             const int s0 = model_seg(b, K, v);
             for (int f : {-1, 0, 1}) {
                 const int seg = f < 0 ? std::max(1, (s0 * 2) / 3) : (f > 0 ? (s0 * 3) / 2 : s0);

@@ -1,496 +1,24 @@
-// Temporally blocked TMz stencil: K leapfrog steps per launch.
-//
-// Work unit: one warp owns a strip of 128 columns (4 per lane, loaded and
-// stored as float4) and a segment of rows [y0, y1). It streams down the rows
-// once; at iteration t it loads level-0 row t and, for k = 0..K-1, advances
-// level k to level k+1 at row t-k-1 (each level lags the one below it by one
-// row, which is exactly the reach of one Yee step in s). The rows of the
-// intermediate levels never leave registers: per level a lane keeps the one
-// pending row (Ez, Hx, Hy and its 4 labels). Only level 0 is read from and
-// level K written to memory (ping-pong buffers), so the DRAM traffic per
-// cell-update falls from 25 bytes to about 25/K plus the halo overhead.
-//
-// Halos: one step moves information one column and one row each way, so a
-// strip computes K (rounded up to 4) extra columns on each side and a
-// segment K extra rows above and below; only the interior is stored.
-// Columns wrap modulo nx (periodic x, Sec. 2.4); the neighbour column of
-// the lane's outer column comes from the adjacent lane by shuffle.
-//
-// P polarisation (POL = 1, TEz in the variables eta0 Hz, -Ex, -Ey) runs the
-// same pipeline with loss-free centre updates and lossy edge updates whose
-// coefficients come from the label pair of each edge: the top edge of row r
-// pairs rows r-1 and r (level k+1 still holds the label word of row r-1 as
-// its pending row; level K keeps one extra word), the left edge of column q
-// pairs columns q-1 and q (the neighbour lane's last label by shuffle).
-//
-// CPML rows (top/bottom P rows) carry their psi recursion from level to
-// level in a per-strip scratch area; the segment plan guarantees that only
-// the first and last segment of a strip ever touch CPML rows. The TF/SF
-// corrections (Sec. 2.5) are applied by every segment that computes row js;
-// DFT accumulation (Sec. 2.6) is done by the segment owning the monitor row,
-// which the plan keeps at least one row above its segment's end.
-#include <cuda_runtime.h>
-
-#include "fdtd_internal.h"
+// Dispatch of the temporally blocked kernels by polarisation; the
+// instances live in blocked_s.cu, blocked_sb.cu and blocked_p.cu (compiled
+// in parallel), the kernel templates in blocked_impl.cuh.
+#include "blocked_impl.cuh"
 
 namespace fdtd {
 
-namespace {
-
-constexpr unsigned FULL = 0xffffffffu;
-
-__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
-    const float4 x = __ldg(reinterpret_cast<const float4*>(p));
-    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
-}
-__device__ __forceinline__ void ld4_rw(const float* p, float (&v)[4]) {
-    const float4 x = *reinterpret_cast<const float4*>(p);
-    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
-}
-__device__ __forceinline__ void st4(float* p, const float (&v)[4]) {
-    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-}
-
-// Asynchronous global -> shared copies (cp.async); `bytes` = 0 zero-fills the
-// destination without reading the source.
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int bytes) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, int bytes) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
-constexpr int kRing = 4;   // rows in flight per warp for code shape 2
-
-}  // namespace
-
-// Register state of one warp's pipeline: per level k the pending row
-// (Ez, Hx, Hy, 4 packed labels); level K keeps Ez and Hx of its last row
-// (and, for POL = 1, its label word).
-template <int K>
-struct Pipe {
-    float E[K + 1][4], X[K + 1][4], Y[K][4];
-    uint32_t L[K + 1];
-};
-
-struct Lane {
-    const float2* coef;
-    int gx, y0, y1, ny, P, nx;
-    bool own, own_r, own_t;
-    float S;
-};
-
-// One iteration of the pipeline: level k advances at row t-k-1, k = 0..K-1.
-// GENERAL = false is the lean path for iterations whose K rows hold no
-// CPML, source, monitor or boundary row and lie inside the valid range;
-// both paths round identically.
-template <int K, bool GENERAL, int POL>
-__device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[4],
-                                        float (&fY)[4], uint32_t& fL, const int t,
-                                        const BlockedArgs& a, const Lane& ln, float* slotE,
-                                        float* slotH, const int64_t n0) {
-    const float S = ln.S;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const int r = t - k - 1;
-        float oE[4], oX[4], oY[4];
-        const uint32_t cL = p.L[k];
-        // P: packed label-pair indices (labels < 16) of the top and left edges
-        uint32_t xP = 0u, yP = 0u;
-        if (POL == 1) {
-            const uint32_t lUp = p.L[k + 1];                          // row r-1
-            const uint32_t lNb = __shfl_up_sync(FULL, cL, 1) >> 24;   // column q-1 of lane 0
-            xP = (lUp << 4) | cL;
-            yP = (((cL << 8) | lNb) << 4) | cL;
-        }
-        bool active = true;
-        if (GENERAL) {
-            const int lo = (ln.y0 == 0) ? 0 : (ln.y0 - K + k);
-            const int hi = min(ln.ny, ln.y1 + K - k - 1);
-            active = (r >= lo && r < hi);
-        }
-        if (active) {
-            const int64_t n = n0 + k;
-            const float yR = __shfl_down_sync(FULL, p.Y[k][0], 1);
-            const bool tf = GENERAL && (r == a.s.js);
-            const float hinc = tf ? a.s.hinc[n] : 0.f;
-            const int pe = GENERAL ? pml_e_index(r, ln.ny, ln.P) : -1;
-            if (GENERAL && pe >= 0) {
-                const float b = a.s.pml_e[pe], c = a.s.pml_e[2 * ln.P + pe];
-                const float ik = a.s.pml_e[4 * ln.P + pe];
-                float psi[4];
-                if (k == 0) ld4(a.psiE_in + (size_t)pe * a.s.pitch + ln.gx, psi);
-                else ld4_rw(slotE + (size_t)pe * 128, psi);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float2 cc = POL ? make_float2(1.0f, S) : ln.coef[(cL >> (8 * q)) & 0xffu];
-                    const float dhy = __fsub_rn(q < 3 ? p.Y[k][q + 1] : yR, p.Y[k][q]);
-                    float dhx = __fsub_rn(fX[q], p.X[k][q]);
-                    if (tf) dhx = __fsub_rn(dhx, hinc);
-                    psi[q] = psi_new(b, c, psi[q], dhx);
-                    oE[q] = ez_new_pml(cc.x, cc.y, p.E[k][q], dhy, dhx, ik, psi[q]);
-                }
-                if (k == K - 1) {
-                    if (ln.own) st4(a.psiE_out + (size_t)pe * a.s.pitch + ln.gx, psi);
-                } else {
-                    st4(slotE + (size_t)pe * 128, psi);
-                }
-            } else {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float2 cc = POL ? make_float2(1.0f, S) : ln.coef[(cL >> (8 * q)) & 0xffu];
-                    const float dhy = __fsub_rn(q < 3 ? p.Y[k][q + 1] : yR, p.Y[k][q]);
-                    float dhx = __fsub_rn(fX[q], p.X[k][q]);
-                    if (tf) dhx = __fsub_rn(dhx, hinc);
-                    oE[q] = ez_new(cc.x, cc.y, p.E[k][q], dhy, dhx);
-                }
-            }
-            if (!GENERAL || r > 0) {
-                const float einc = tf ? a.s.einc[n] : 0.f;
-                const int ph = GENERAL ? pml_h_index(r, ln.ny, ln.P) : -1;
-                if (GENERAL && ph >= 0) {
-                    const float b = a.s.pml_h[ph], c = a.s.pml_h[2 * ln.P + ph];
-                    const float ik = a.s.pml_h[4 * ln.P + ph];
-                    float psi[4];
-                    if (k == 0) ld4(a.psiH_in + (size_t)ph * a.s.pitch + ln.gx, psi);
-                    else ld4_rw(slotH + (size_t)ph * 128, psi);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        float d = __fsub_rn(oE[q], p.E[k + 1][q]);
-                        if (tf) d = __fsub_rn(d, einc);
-                        psi[q] = psi_new(b, c, psi[q], d);
-                        if (POL == 1) {
-                            const float2 cx = ln.coef[(xP >> (8 * q)) & 0xffu];
-                            oX[q] = e_edge_new_pml(cx.x, cx.y, p.X[k][q], d, ik, psi[q]);
-                        } else {
-                            oX[q] = h_new_pml(p.X[k][q], S, d, ik, psi[q]);
-                        }
-                    }
-                    if (k == K - 1) {
-                        if (ln.own) st4(a.psiH_out + (size_t)ph * a.s.pitch + ln.gx, psi);
-                    } else {
-                        st4(slotH + (size_t)ph * 128, psi);
-                    }
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        float d = __fsub_rn(oE[q], p.E[k + 1][q]);
-                        if (tf) d = __fsub_rn(d, einc);
-                        if (POL == 1) {
-                            const float2 cx = ln.coef[(xP >> (8 * q)) & 0xffu];
-                            oX[q] = e_edge_new(cx.x, cx.y, p.X[k][q], d);
-                        } else {
-                            oX[q] = h_new(p.X[k][q], S, d);
-                        }
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) oX[q] = p.X[k][q];
-            }
-            const float eL = __shfl_up_sync(FULL, oE[3], 1);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float dy = __fsub_rn(oE[q], q > 0 ? oE[q - 1] : eL);
-                if (POL == 1) {
-                    const float2 cy = ln.coef[(yP >> (8 * q)) & 0xffu];
-                    oY[q] = e_edge_new(cy.x, cy.y, p.Y[k][q], dy);
-                } else {
-                    oY[q] = h_new(p.Y[k][q], S, dy);
-                }
-            }
-            if (GENERAL && ln.own) {
-                if (ln.own_r && r == a.s.jr) {
-                    const double2 ph = a.s.phE[n];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) dft_add(&a.s.dft[ln.gx + q], oE[q], ph);
-                }
-                if (ln.own_r && r == a.s.jr + 1) {
-                    const double2 ph = a.s.phH[n];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        dft_add(&a.s.dft[ln.nx + ln.gx + q], hx_avg(p.X[k + 1][q], oX[q]), ph);
-                }
-                if (ln.own_t && r == a.s.jt) {
-                    const double2 ph = a.s.phE[n];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        dft_add(&a.s.dft[2 * ln.nx + ln.gx + q], oE[q], ph);
-                }
-                if (ln.own_t && r == a.s.jt + 1) {
-                    const double2 ph = a.s.phH[n];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        dft_add(&a.s.dft[3 * ln.nx + ln.gx + q], hx_avg(p.X[k + 1][q], oX[q]),
-                                ph);
-                }
-            }
-        } else {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) { oE[q] = 0.f; oX[q] = 0.f; oY[q] = 0.f; }
-        }
-        // level k now waits at row r+1; the new level-(k+1) row r flows up
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            p.E[k][q] = fE[q]; p.X[k][q] = fX[q]; p.Y[k][q] = fY[q];
-            fE[q] = oE[q]; fX[q] = oX[q]; fY[q] = oY[q];
-        }
-        p.L[k] = fL;
-        fL = cL;
-        if (POL == 1 && k == K - 1) p.L[K] = cL;
-    }
-}
-
-// One warp task: strip `task % n_strips` of segment `task / n_strips`.
-// Code shapes V: 0 one row per loop trip with a one-row register prefetch;
-// 1 two rows per loop trip on plain stretches; 2 level-0 rows streamed
-// through a shared-memory ring filled kRing rows ahead by cp.async.
-template <int K, int V, int POL>
-__device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float2* s_coef,
-                                             const int task, const int64_t n0) {
-    constexpr int H = ((K + 3) / 4) * 4;
-    const int lane = threadIdx.x & 31;
-    const int strip = task % a.n_strips;
-    const int seg = task / a.n_strips;
-    Lane ln;
-    ln.coef = s_coef;
-    ln.y0 = a.seg_y0[seg];
-    ln.y1 = a.seg_y0[seg + 1];
-    ln.nx = a.s.nx; ln.ny = a.s.ny; ln.P = a.s.P; ln.S = a.s.S;
-    const size_t pitch = (size_t)a.s.pitch;
-    const size_t lpitch = (size_t)a.s.lpitch;
-    const int xl = 4 * lane;                        // local column of the lane
-    const int xg_pre = strip * a.w_int - H + xl;    // global column before wrapping
-    ln.gx = ((xg_pre % ln.nx) + ln.nx) % ln.nx;     // nx % 4 == 0: 4 columns stay contiguous
-    ln.own = (xl >= H) && (xl < H + a.w_int) && (xg_pre < ln.nx);
-    ln.own_r = (a.s.jr >= ln.y0) && (a.s.jr < ln.y1);
-    ln.own_t = (a.s.jt >= ln.y0) && (a.s.jt < ln.y1);
-    float* slotE = a.slotE + (size_t)strip * 2 * ln.P * 128 + xl;
-    float* slotH = a.slotH + (size_t)strip * 2 * ln.P * 128 + xl;
-
-    Pipe<K> p;
-#pragma unroll
-    for (int k = 0; k <= K; ++k) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            p.E[k][q] = 0.f; p.X[k][q] = 0.f;
-            if (k < K) p.Y[k][q] = 0.f;
-        }
-        p.L[k] = 0u;
-    }
-
-    const int y0 = ln.y0, y1 = ln.y1, ny = ln.ny, P = ln.P;
-    const int t_begin = (y0 == 0) ? 0 : (y0 - K);
-    const int t_end = y1 + K;
-    // iterations whose rows t-K .. t-1 are all plain interior rows
-    const int fast_lo = max(max(y0 + K - 1, K + 1), P + K);
-    const int fast_hi = ny - P + 1;
-    const int sp[5] = {a.s.js, a.s.jr, a.s.jr + 1, a.s.jt, a.s.jt + 1};
-    auto is_fast = [&](int t) {
-        bool f = (t >= fast_lo) && (t < fast_hi);
-#pragma unroll
-        for (int s = 0; s < 5; ++s) f = f && ((unsigned)(t - sp[s] - 1) >= (unsigned)K);
-        return f;
-    };
-
-    auto finish = [&](const int t, float (&fE)[4], float (&fX)[4], float (&fY)[4]) {
-        const int ro = t - K;
-        if (ln.own && ro >= y0 && ro < y1) {
-            const size_t o = (size_t)ro * pitch + ln.gx;
-            st4(a.ez_out + o, fE);
-            st4(a.hx_out + o, fX);
-            st4(a.hy_out + o, fY);
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) { p.E[K][q] = fE[q]; p.X[K][q] = fX[q]; }
-    };
-
-    if (V == 2) {
-        __shared__ float4 ring[kRing][3][32];
-        __shared__ uint32_t ring_l[kRing][32];
-        auto issue = [&](const int row, const int slot) {
-            const bool ok = row < ny;
-            const size_t o = (size_t)(ok ? row : 0) * pitch + ln.gx;
-            const int nb = ok ? 16 : 0;
-            cp_async16(&ring[slot][0][lane], a.ez_in + o, nb);
-            cp_async16(&ring[slot][1][lane], a.hx_in + o, nb);
-            cp_async16(&ring[slot][2][lane], a.hy_in + o, nb);
-            cp_async4(&ring_l[slot][lane], a.s.labels + (size_t)(ok ? row : 0) * lpitch + ln.gx,
-                      ok ? 4 : 0);
-            cp_async_commit();
-        };
-#pragma unroll
-        for (int d = 0; d < kRing; ++d) issue(t_begin + d, d);
-        int slot = 0;
-#pragma unroll 1
-        for (int t = t_begin; t < t_end; ++t) {
-            cp_async_wait<kRing - 1>();
-            float fE[4], fX[4], fY[4];
-            const float4 e4 = ring[slot][0][lane], x4 = ring[slot][1][lane], y4 = ring[slot][2][lane];
-            uint32_t fL = ring_l[slot][lane];
-            fE[0] = e4.x; fE[1] = e4.y; fE[2] = e4.z; fE[3] = e4.w;
-            fX[0] = x4.x; fX[1] = x4.y; fX[2] = x4.z; fX[3] = x4.w;
-            fY[0] = y4.x; fY[1] = y4.y; fY[2] = y4.z; fY[3] = y4.w;
-            issue(t + kRing, slot);
-            slot = (slot + 1 == kRing) ? 0 : slot + 1;
-            if (is_fast(t)) advance<K, false, POL>(p, fE, fX, fY, fL, t, a, ln, slotE, slotH, n0);
-            else advance<K, true, POL>(p, fE, fX, fY, fL, t, a, ln, slotE, slotH, n0);
-            finish(t, fE, fX, fY);
-        }
-        cp_async_wait<0>();
-        return;
-    }
-
-    // software pipeline: row t+1 is fetched while row t is processed
-    float nE[4], nX[4], nY[4];
-    uint32_t nL = 0u;
-    {
-        const size_t o = (size_t)t_begin * pitch + ln.gx;
-        ld4(a.ez_in + o, nE);
-        ld4(a.hx_in + o, nX);
-        ld4(a.hy_in + o, nY);
-        nL = __ldg(reinterpret_cast<const uint32_t*>(a.s.labels + (size_t)t_begin * lpitch + ln.gx));
-    }
-    auto iteration = [&](const int t, const bool fast) {
-        float fE[4], fX[4], fY[4];
-        uint32_t fL = nL;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) { fE[q] = nE[q]; fX[q] = nX[q]; fY[q] = nY[q]; }
-        if (t + 1 < ny) {
-            const size_t o = (size_t)(t + 1) * pitch + ln.gx;
-            ld4(a.ez_in + o, nE);
-            ld4(a.hx_in + o, nX);
-            ld4(a.hy_in + o, nY);
-            nL = __ldg(reinterpret_cast<const uint32_t*>(a.s.labels + (size_t)(t + 1) * lpitch + ln.gx));
-        } else {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) { nE[q] = 0.f; nX[q] = 0.f; nY[q] = 0.f; }
-            nL = 0u;
-        }
-        if (fast) advance<K, false, POL>(p, fE, fX, fY, fL, t, a, ln, slotE, slotH, n0);
-        else advance<K, true, POL>(p, fE, fX, fY, fL, t, a, ln, slotE, slotH, n0);
-        finish(t, fE, fX, fY);
-    };
-    int t = t_begin;
-#pragma unroll 1
-    while (t < t_end) {
-        if (V == 1 && t + 1 < t_end && is_fast(t) && is_fast(t + 1)) {
-            iteration(t, true);
-            iteration(t + 1, true);
-            t += 2;
-        } else {
-            if (is_fast(t)) iteration(t, true);
-            else iteration(t, false);
-            t += 1;
-        }
-    }
-}
-
-template <int K, int V, int POL>
-__global__ void __launch_bounds__(32) k_blocked(const BlockedArgs a, const int64_t n0) {
-    __shared__ float2 s_coef[256];
-    const int n_coef = POL ? 256 : a.s.n_labels;
-    for (int t = threadIdx.x; t < n_coef; t += blockDim.x) s_coef[t] = a.s.coef[t];
-    __syncwarp();
-    if ((int)blockIdx.x >= a.n_tasks) return;       // one warp per block and task
-    blocked_task<K, V, POL>(a, s_coef, blockIdx.x, n0);
-}
-
-// Many independent simulations in one launch: the grid covers the union of
-// their warp tasks. Each block finds its simulation, copies that
-// simulation's arguments (ping-pong orientation `parity`) to shared memory
-// and runs the same task body. The absolute step of the launch is
-// n_base(sim) + *step_base + step_off, so a captured chunk of launches can be
-// replayed with a new *step_base.
-template <int K, int V, int POL>
-__global__ void __launch_bounds__(32) k_blocked_batch(const BatchArgs b, const int step_off,
-                                                      const int parity) {
-    __shared__ float2 s_coef[256];
-    __shared__ __align__(16) unsigned char s_raw[sizeof(BlockedArgs)];
-    const int task = blockIdx.x;
-    if (task >= b.n_tasks) return;
-    const int sim = b.task_sim[task];
-    const BlockedArgs* src = b.sims + (size_t)parity * b.n_sims + sim;
-    const int* w = reinterpret_cast<const int*>(src);
-    int* d = reinterpret_cast<int*>(s_raw);
-    for (int q = threadIdx.x; q < (int)(sizeof(BlockedArgs) / sizeof(int)); q += 32) d[q] = w[q];
-    __syncwarp();
-    const BlockedArgs& a = *reinterpret_cast<const BlockedArgs*>(s_raw);
-    const int n_coef = POL ? 256 : a.s.n_labels;
-    for (int t = threadIdx.x; t < n_coef; t += 32) s_coef[t] = a.s.coef[t];
-    __syncwarp();
-    const int64_t n0 = a.n_base + *b.step_base + step_off;
-    blocked_task<K, V, POL>(a, s_coef, task - b.first_task[sim], n0);
-}
-
-template <int K, int V, int POL>
-static int occupancy_warps() {
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_blocked<K, V, POL>, 32, 0) != cudaSuccess)
-        return 0;
-    return b;
-}
-
 int blocked_max_K() { return 8; }
 
-#define FDTD_BLOCKED_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8)
-
-// P polarisation is built for code shape 2 only; other shapes map to it.
 int blocked_warps_per_sm(int K, int variant, int pol) {
-    switch (K) {
-#define X(k)                                                                  \
-    case k:                                                                   \
-        if (pol) return occupancy_warps<k, 2, 1>();                           \
-        return variant == 2 ? occupancy_warps<k, 2, 0>()                      \
-                            : (variant ? occupancy_warps<k, 1, 0>() : occupancy_warps<k, 0, 0>());
-        FDTD_BLOCKED_CASES(X)
-#undef X
-        default: return 0;
-    }
+    return pol ? blocked_occupancy_p(K, variant) : blocked_occupancy_s(K, variant);
+}
+
+bool launch_blocked(const BlockedArgs& a, int K, int variant, int64_t n0, cudaStream_t st) {
+    return a.s.pol ? launch_blocked_p(a, K, variant, n0, st) : launch_blocked_s(a, K, variant, n0, st);
 }
 
 bool launch_blocked_batch(const BatchArgs& b, int K, int variant, int step_off, int parity,
                           int pol, cudaStream_t st) {
-    const unsigned grid = (unsigned)b.n_tasks;
-    switch (K) {
-#define X(k)                                                                                   \
-    case k:                                                                                    \
-        if (pol) k_blocked_batch<k, 2, 1><<<grid, 32, 0, st>>>(b, step_off, parity);           \
-        else if (variant == 2) k_blocked_batch<k, 2, 0><<<grid, 32, 0, st>>>(b, step_off, parity); \
-        else if (variant) k_blocked_batch<k, 1, 0><<<grid, 32, 0, st>>>(b, step_off, parity);  \
-        else k_blocked_batch<k, 0, 0><<<grid, 32, 0, st>>>(b, step_off, parity);               \
-        break;
-        FDTD_BLOCKED_CASES(X)
-#undef X
-        default: return false;
-    }
-    return true;
-}
-
-bool launch_blocked(const BlockedArgs& a, int K, int variant, int64_t n0, cudaStream_t st) {
-    const unsigned grid = (unsigned)a.n_tasks;
-    switch (K) {
-#define X(k)                                                                  \
-    case k:                                                                   \
-        if (a.s.pol) k_blocked<k, 2, 1><<<grid, 32, 0, st>>>(a, n0);          \
-        else if (variant == 2) k_blocked<k, 2, 0><<<grid, 32, 0, st>>>(a, n0); \
-        else if (variant) k_blocked<k, 1, 0><<<grid, 32, 0, st>>>(a, n0);     \
-        else k_blocked<k, 0, 0><<<grid, 32, 0, st>>>(a, n0);                  \
-        break;
-        FDTD_BLOCKED_CASES(X)
-#undef X
-        default: return false;
-    }
-    return true;
+    return pol ? launch_blocked_batch_p(b, K, variant, step_off, parity, st)
+               : launch_blocked_batch_s(b, K, variant, step_off, parity, st);
 }
 
 }  // namespace fdtd

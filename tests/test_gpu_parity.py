@@ -90,7 +90,8 @@ def test_config1b_fields_and_rt(fd, ref_c1b, kernel, K):
                                            (7, 40, 1), (5, 23, 1), (4, 31, 0), (2, 19, 1),
                                            (1, 17, 1), (6, 200, 0), (6, 33, 1), (3, 29, 1),
                                            (8, None, 2), (8, 27, 2), (7, 41, 2), (5, 19, 2),
-                                           (3, 22, 2), (1, 18, 2)])
+                                           (3, 22, 2), (1, 18, 2), (8, None, 3), (7, None, 3),
+                                           (7, 41, 3), (6, 33, 3), (4, 31, 3), (1, 18, 3)])
 def test_blocked_is_bitwise_equal_to_naive(fd, K, seg, variant):
     spec = config_c1b(steps=411)
     with fd.Simulation(spec, kernel=1) as a:

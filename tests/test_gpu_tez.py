@@ -54,13 +54,15 @@ def test_config1b_p_fields_and_rt(fd, ref_c1b_p, kernel, K):
     assert abs(R - rt[0]) < 1e-4 and abs(T - rt[1]) < 1e-4
 
 
+@pytest.mark.parametrize("variant", [2, 3])
 @pytest.mark.parametrize("K,seg", [(8, None), (8, 27), (7, 41), (5, 19), (3, 22), (1, 18)])
-def test_p_blocked_is_bitwise_equal_to_naive(fd, K, seg):
+def test_p_blocked_is_bitwise_equal_to_naive(fd, K, seg, variant):
     spec = config_c1b(steps=411).with_(polarization=POL_P)
     with fd.Simulation(spec, kernel=1) as a:
         a.run(411)
         fa, da = a.fields(), a.dft()
     with fd.Simulation(spec, kernel=2, block_steps=K, seg_rows=seg) as b:
+        fd.fdtd_set_option(b.h, fd.FDTD_OPT_VARIANT, variant)
         b.run(200)
         b.run(211)
         fb, db = b.fields(), b.dft()
