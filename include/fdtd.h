@@ -127,14 +127,14 @@ typedef struct fdtd_stats {
 
 /* Options for fdtd_set_option. */
 #define FDTD_OPT_KERNEL 1      /* 0 auto, 1 per-half-step kernels, 2 temporally blocked */
-#define FDTD_OPT_BLOCK_STEPS 2 /* steps per blocked launch, 1..8 (default 7) */
+#define FDTD_OPT_BLOCK_STEPS 2 /* steps per blocked launch, 1..8 (default 8) */
 #define FDTD_OPT_SEG_ROWS 3    /* rows per warp task of the blocked kernel (0 = auto) */
 #define FDTD_OPT_TIMING 4      /* 1: time stencil launches with CUDA events */
 #define FDTD_OPT_WATCHDOG 5    /* check fields for non-finite values every N steps (0 off) */
 #define FDTD_OPT_VARIANT 6     /* blocked-kernel code shape: 0 one row per loop trip with a register
                                   prefetch, 1 two rows per trip, 2 rows streamed through a
-                                  shared-memory ring by cp.async, 3 shape 2 built under a
-                                  224-register cap (default); P handles run shapes 2 and 3 */
+                                  shared-memory ring by cp.async (default), 3 shape 2 built
+                                  under a 224-register cap; P handles run shapes 2 and 3 */
 #define FDTD_OPT_GRAPH 7       /* batches: replay captured CUDA graphs of launch chunks (default 1) */
 
 /* Create a simulation. grid, labels (ny*nx uint8, values < n_labels), table

@@ -163,17 +163,100 @@ int sm_count(fdtd_handle* h) {
 // Row boundaries of the warp-task segments: `seg` rows each; the last
 // segment absorbs a remainder shorter than min_seg; no boundary may fall
 // just below a monitor row (the owning segment needs the row below it).
+// Cost of a general-path iteration of the blocked kernel in lean
+// iterations, as used by the segment planner. Measured on GB300 (config 2,
+// both polarisations): 7.5 balances the tasks best; the pipeline is
+// issue-bound and the general path (CPML recursion through the per-strip
+// carry, source and monitor terms, row checks) costs several lean ones.
+constexpr double kGeneralCost = 7.5;
+
+// Estimated cost of one pipeline iteration t of the warp task of a segment
+// starting at y0: the kernel's lean-path test (blocked_task, is_fast) gives
+// 1, the general path `wg` lean iterations. A segment [y0, y1) runs the
+// iterations t_begin(y0) .. y1+K-1.
+double iteration_cost(const fdtd_grid& g, int K, int t, double wg) {
+    const int P = g.pml_cells;
+    bool f = (t >= std::max(K + 1, P + K)) && (t < g.ny - P + 1);
+    const int sp[5] = {g.tfsf_row, g.r_row, g.r_row + 1, g.t_row, g.t_row + 1};
+    for (int q = 0; q < 5 && f; ++q) f = (unsigned)(t - sp[q] - 1) >= (unsigned)K;
+    return f ? 1.0 : wg;
+}
+
+// Segment boundaries for about ny/seg segments of equal estimated cost. Only
+// the first and last segment may reach the CPML rows (both hold at least
+// min_seg = P + K + 1 rows), and no boundary falls on r_row + 1 or
+// t_row + 1 (the segment owning a monitor row also owns the row below it,
+// whose Hx enters the row average).
 std::vector<int> segment_bounds(const fdtd_grid& g, int seg, int min_seg) {
-    std::vector<int> b{0};
-    int pos = seg;
-    while (pos < g.ny) {
-        if (pos == g.r_row + 1 || pos == g.t_row + 1) ++pos;
-        if (g.ny - pos < min_seg) break;
-        b.push_back(pos);
-        pos += seg;
+    const int ny = g.ny;
+    const int K = min_seg - g.pml_cells - 1;
+    const int n_target = std::max(1, (int)std::lround((double)ny / std::max(seg, 1)));
+    const double wg = kGeneralCost;
+    // prefix sums of the iteration costs: a segment [y0, y1) costs
+    // C(y1 + K) - C(t_begin(y0))
+    std::vector<double> C((size_t)ny + K + 1, 0.0);
+    for (int t = 0; t < ny + K; ++t) C[(size_t)t + 1] = C[(size_t)t] + iteration_cost(g, K, t, wg);
+    auto cost = [&](int y0, int y1) { return C[(size_t)y1 + K] - C[(size_t)(y0 == 0 ? 0 : y0 - K)]; };
+    auto ok_cut = [&](int y) {
+        return y >= min_seg && ny - y >= min_seg && y != g.r_row + 1 && y != g.t_row + 1;
+    };
+    // greedy cut with every segment cost <= T; empty when more than
+    // n_target segments would be needed
+    auto cut = [&](double T) {
+        std::vector<int> b{0};
+        int y0 = 0;
+        while (cost(y0, ny) > T) {
+            int best = -1;
+            for (int y1 = y0 + 1; y1 <= ny - min_seg; ++y1) {
+                if (cost(y0, y1) > T) break;
+                if (ok_cut(y1)) best = y1;
+            }
+            if (best < 0 || (int)b.size() >= n_target) return std::vector<int>();
+            b.push_back(best);
+            y0 = best;
+        }
+        b.push_back(ny);
+        return b;
+    };
+    double lo = 0.0, hi = cost(0, ny);
+    std::vector<int> best{0, ny};
+    for (int it = 0; it < 50 && hi - lo > 0.25; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        std::vector<int> b = cut(mid);
+        if (b.empty()) {
+            lo = mid;
+        } else {
+            hi = mid;
+            best = b;
+        }
     }
-    b.push_back(g.ny);
-    return b;
+    // The first and last segments (all CPML rows) can bound the maximum
+    // cost; use the rest of the segment budget anyway, splitting the
+    // costliest splittable segment where its halves cost the same (the
+    // maximum does not grow, the tasks fill the GPU).
+    while ((int)best.size() - 1 < n_target) {
+        int pick = -1, at = -1;
+        double pick_cost = -1.0;
+        for (size_t q = 0; q + 1 < best.size(); ++q) {
+            const int y0 = best[q], y1 = best[q + 1];
+            const double c = cost(y0, y1);
+            if (c <= pick_cost) continue;
+            int m = -1;
+            double bal = 1e300;
+            for (int y = y0 + 1; y < y1; ++y) {
+                if (!ok_cut(y)) continue;
+                const double d = std::fabs(cost(y0, y) - cost(y, y1));
+                if (d < bal) { bal = d; m = y; }
+            }
+            if (m < 0) continue;
+            pick = (int)q;
+            at = m;
+            pick_cost = c;
+        }
+        if (pick < 0) break;
+        best.insert(best.begin() + pick + 1, at);
+    }
+    return best;
 }
 
 // Segment plan of the blocked kernel for depth K (see blocked.cu). One warp

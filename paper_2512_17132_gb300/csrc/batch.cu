@@ -34,7 +34,7 @@ struct fdtd_batch {
     int device = 0;
     cudaStream_t stream = nullptr, side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_in = nullptr;
-    int K = 7, variant = 3, seg = 0, timing = 0, use_graph = 1;
+    int K = 8, variant = 2, seg = 0, timing = 0, use_graph = 1;
     // plan
     bool planned = false;
     int pK = 0, pvar = -1, pseg = -1, seg_used = 0;

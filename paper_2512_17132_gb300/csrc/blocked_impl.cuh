@@ -296,8 +296,13 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float2*
     const int y0 = ln.y0, y1 = ln.y1, ny = ln.ny, P = ln.P;
     const int t_begin = (y0 == 0) ? 0 : (y0 - K);
     const int t_end = y1 + K;
-    // iterations whose rows t-K .. t-1 are all plain interior rows
-    const int fast_lo = max(max(y0 + K - 1, K + 1), P + K);
+    // Iterations whose rows t-K .. t-1 hold no CPML, source or monitor row
+    // take the lean path. That includes the first iterations of a segment,
+    // where some levels are still outside their valid row range: the lean
+    // path computes values there that no stored row ever depends on (each
+    // level's valid range shrinks by one row per step, exactly the reach of
+    // a step), and it has no other side effect.
+    const int fast_lo = max(K + 1, P + K);
     const int fast_hi = ny - P + 1;
     const int sp[5] = {a.s.js, a.s.jr, a.s.jr + 1, a.s.jt, a.s.jt + 1};
     auto is_fast = [&](int t) {
@@ -415,10 +420,10 @@ __global__ void __launch_bounds__(32) k_blocked(const BlockedArgs a, const int64
     blocked_kernel_body<K, V, POL>(a, n0);
 }
 
-// Code shape 3: shape 2 compiled under a 224-register cap. Measured on
-// GB300 it issues faster than the uncapped build at the same occupancy
-// (8 one-warp blocks per SM at K = 7 and 8; tighter caps that admit 10 or 11
-// blocks per SM, and 9-block segment plans, were slower).
+// Code shape 3: shape 2 compiled under a 224-register cap (8 one-warp
+// blocks per SM, as the uncapped build). With equal-height segments it was
+// 1-2 % faster than shape 2; with the cost-balanced segment plan shape 2 at
+// K = 8 is faster, and shape 3 stays available as an option.
 template <int K, int POL>
 __global__ void __maxnreg__(224) k_blocked_cap(const BlockedArgs a,
                                                                      const int64_t n0) {

@@ -169,7 +169,7 @@ struct fdtd_handle {
     // blocked-kernel plans per depth
     std::vector<fdtd::BlockPlan> plans;
     // options
-    int opt_kernel = 0, opt_block = 7, opt_seg = 0, opt_timing = 0, opt_variant = 3;
+    int opt_kernel = 0, opt_block = 8, opt_seg = 0, opt_timing = 0, opt_variant = 2;
     int64_t opt_watchdog = 0;
     // stats
     int64_t n = 0;
