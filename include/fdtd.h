@@ -309,12 +309,12 @@ void fdtd_batch_destroy(fdtd_batch* b);
  *
  * Advances a source-free field state by `steps` (1..8) leapfrog steps with
  * the temporally blocked kernel, on `cuda_stream` (NULL = legacy stream), and
- * allocates nothing: the kernel's scratch (CPML carries between time levels,
- * segment table, coefficient and CPML tables, zeroed source tables, a sink
- * for monitor sums) lives in one static 8 MiB device array per GPU, held by
- * every GPU that loads the library until the process exits. Grids needing
- * more scratch (roughly nx * (pml_cells + 1) > 300000, or pml_cells > 64)
- * are rejected with FDTD_EINVAL and a message.
+ * allocates nothing: the kernel's scratch (segment table, coefficient and
+ * CPML tables, zeroed source tables, a sink for monitor sums) lives in one
+ * static 8 MiB device array per GPU, held by every GPU that loads the
+ * library until the process exits. Grids needing more scratch (roughly
+ * nx > 130000, or pml_cells > 64) are rejected with FDTD_EINVAL and a
+ * message.
  *   grid: layout as for fdtd_create (nx % 4 == 0 required); table/n_labels/
  *     lambda0: materials at the wavelength (coefficients as in fdtd_create);
  *   labels: device, ny*nx uint8, values < n_labels (not checked here);

@@ -308,7 +308,6 @@ void step_out_of_place(fdtd_handle* h, const StateView& in, const StateView& out
             b.ez_in = in.E; b.hx_in = in.X; b.hy_in = in.Y;
             b.ez_out = out.E; b.hx_out = out.X; b.hy_out = out.Y;
             b.psiE_in = in.PE; b.psiH_in = in.PH; b.psiE_out = out.PE; b.psiH_out = out.PH;
-            b.slotE = h->slotE; b.slotH = h->slotH;
             b.seg_y0 = pl->d_seg_y0;
             b.n_strips = pl->n_strips;
             b.n_tasks = pl->n_strips * pl->n_segs;

@@ -160,14 +160,12 @@ int sm_count(fdtd_handle* h) {
     return v;
 }
 
-// Row boundaries of the warp-task segments: `seg` rows each; the last
-// segment absorbs a remainder shorter than min_seg; no boundary may fall
-// just below a monitor row (the owning segment needs the row below it).
 // Cost of a general-path iteration of the blocked kernel in lean
-// iterations, as used by the segment planner. Measured on GB300 (config 2,
-// both polarisations): 7.5 balances the tasks best; the pipeline is
-// issue-bound and the general path (CPML recursion through the per-strip
-// carry, source and monitor terms, row checks) costs several lean ones.
+// iterations, as used by the segment planner. Measured on GB300: 7.5
+// balances the tasks best on config 2 (both polarisations) and is within
+// run-to-run noise of the best weight on the 6000-row config 5; the pipeline
+// is issue-bound and the general path (CPML recursion, source and monitor
+// terms, row checks) costs several lean ones.
 constexpr double kGeneralCost = 7.5;
 
 // Estimated cost of one pipeline iteration t of the warp task of a segment
@@ -182,14 +180,13 @@ double iteration_cost(const fdtd_grid& g, int K, int t, double wg) {
     return f ? 1.0 : wg;
 }
 
-// Segment boundaries for about ny/seg segments of equal estimated cost. Only
-// the first and last segment may reach the CPML rows (both hold at least
-// min_seg = P + K + 1 rows), and no boundary falls on r_row + 1 or
-// t_row + 1 (the segment owning a monitor row also owns the row below it,
-// whose Hx enters the row average).
-std::vector<int> segment_bounds(const fdtd_grid& g, int seg, int min_seg) {
+// Segment boundaries for about ny/seg segments of equal estimated cost for
+// K steps per launch. Every boundary lies in [K, ny) (a segment's K halo
+// rows above it exist) and none falls on r_row + 1 or t_row + 1 (the
+// segment owning a monitor row also owns the row below it, whose Hx enters
+// the row average).
+std::vector<int> segment_bounds(const fdtd_grid& g, int seg, int K) {
     const int ny = g.ny;
-    const int K = min_seg - g.pml_cells - 1;
     const int n_target = std::max(1, (int)std::lround((double)ny / std::max(seg, 1)));
     const double wg = kGeneralCost;
     // prefix sums of the iteration costs: a segment [y0, y1) costs
@@ -198,7 +195,7 @@ std::vector<int> segment_bounds(const fdtd_grid& g, int seg, int min_seg) {
     for (int t = 0; t < ny + K; ++t) C[(size_t)t + 1] = C[(size_t)t] + iteration_cost(g, K, t, wg);
     auto cost = [&](int y0, int y1) { return C[(size_t)y1 + K] - C[(size_t)(y0 == 0 ? 0 : y0 - K)]; };
     auto ok_cut = [&](int y) {
-        return y >= min_seg && ny - y >= min_seg && y != g.r_row + 1 && y != g.t_row + 1;
+        return y >= K && y >= 1 && y < ny && y != g.r_row + 1 && y != g.t_row + 1;
     };
     // greedy cut with every segment cost <= T; empty when more than
     // n_target segments would be needed
@@ -207,7 +204,7 @@ std::vector<int> segment_bounds(const fdtd_grid& g, int seg, int min_seg) {
         int y0 = 0;
         while (cost(y0, ny) > T) {
             int best = -1;
-            for (int y1 = y0 + 1; y1 <= ny - min_seg; ++y1) {
+            for (int y1 = y0 + 1; y1 < ny; ++y1) {
                 if (cost(y0, y1) > T) break;
                 if (ok_cut(y1)) best = y1;
             }
@@ -230,7 +227,7 @@ std::vector<int> segment_bounds(const fdtd_grid& g, int seg, int min_seg) {
             best = b;
         }
     }
-    // The first and last segments (all CPML rows) can bound the maximum
+    // Segments the layout rules keep from splitting can bound the maximum
     // cost; use the rest of the segment budget anyway, splitting the
     // costliest splittable segment where its halves cost the same (the
     // maximum does not grow, the tasks fill the GPU).
@@ -278,8 +275,7 @@ BlockPlan& get_plan(fdtd_handle* h, int K) {
     p.halo = (K + 3) / 4 * 4;
     p.w_int = 128 - 2 * p.halo;
     p.n_strips = (g.nx + p.w_int - 1) / p.w_int;
-    const int P = g.pml_cells;
-    const int min_seg = P + K + 1;
+    const int min_seg = K + 1;
     int seg = want_seg;
     if (seg <= 0) {
         int per_sm = blocked_warps_per_sm(K, h->opt_variant, h->src.polarization);
@@ -300,19 +296,11 @@ BlockPlan& get_plan(fdtd_handle* h, int K) {
         }
     }
     seg = std::max(seg, min_seg);
-    const std::vector<int> b = segment_bounds(g, seg, min_seg);
+    const std::vector<int> b = segment_bounds(g, seg, K);
     p.n_segs = (int)b.size() - 1;
     p.seg_rows = seg;
     CK(cudaMalloc(&p.d_seg_y0, b.size() * sizeof(int)));
     CK(cudaMemcpy(p.d_seg_y0, b.data(), b.size() * sizeof(int), cudaMemcpyHostToDevice));
-    const size_t slot = (size_t)p.n_strips * 2 * std::max(P, 1) * 128;
-    if (slot > h->slot_floats) {
-        CK(cudaStreamSynchronize(h->stream));
-        dfree(h->slotE); dfree(h->slotH);
-        CK(cudaMalloc(&h->slotE, slot * sizeof(float)));
-        CK(cudaMalloc(&h->slotH, slot * sizeof(float)));
-        h->slot_floats = slot;
-    }
     return p;
 }
 
@@ -350,7 +338,6 @@ void run_stencil(fdtd_handle* h, int64_t s, int64_t e, int kern) {
         b.ez_out = h->ez[o]; b.hx_out = h->hx[o]; b.hy_out = h->hy[o];
         b.psiE_in = h->psiE[c]; b.psiH_in = h->psiH[c];
         b.psiE_out = h->psiE[o]; b.psiH_out = h->psiH[o];
-        b.slotE = h->slotE; b.slotH = h->slotH;
         b.seg_y0 = p.d_seg_y0;
         b.n_strips = p.n_strips;
         b.n_tasks = p.n_strips * p.n_segs;
@@ -421,7 +408,7 @@ void free_all(fdtd_handle* h) {
     for (auto& c : h->ck) dfree(c);
     h->ck.clear();
     dfree(h->tw_ez); dfree(h->tw_hx); dfree(h->tw_psiE); dfree(h->tw_psiH); dfree(h->tw_dft);
-    dfree(h->d_flux); dfree(h->d_flag); dfree(h->slotE); dfree(h->slotH);
+    dfree(h->d_flux); dfree(h->d_flag);
     dfree(h->d_hinc); dfree(h->d_einc); dfree(h->d_phE); dfree(h->d_phH);
     if (h->h_flux) cudaFreeHost(h->h_flux);
     if (h->h_hinc) cudaFreeHost(h->h_hinc);

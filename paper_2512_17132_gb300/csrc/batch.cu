@@ -45,9 +45,6 @@ struct fdtd_batch {
     TwinArgs* d_twin = nullptr;
     int* d_task_sim = nullptr;
     int* d_first_task = nullptr;
-    float* d_slotE = nullptr;
-    float* d_slotH = nullptr;
-    std::vector<size_t> slot_off;
     int64_t* d_step_base = nullptr;
     double2* d_dummy = nullptr;
     // captured chunk
@@ -97,7 +94,6 @@ void drop_plan(fdtd_batch* b) {
     for (auto& p : b->d_seg) bfree(p);
     b->d_seg.clear();
     bfree(b->d_args); bfree(b->d_twin); bfree(b->d_task_sim); bfree(b->d_first_task);
-    bfree(b->d_slotE); bfree(b->d_slotH);
     b->planned = false;
 }
 
@@ -109,7 +105,7 @@ int model_seg(fdtd_batch* b, int K, int variant) {
     const int w_int = 128 - 2 * ((K + 3) / 4 * 4);
     int min_seg = 1, max_ny = 1;
     for (auto* h : b->hs) {
-        min_seg = std::max(min_seg, h->g.pml_cells + K + 1);
+        min_seg = std::max(min_seg, K + 1);
         max_ny = std::max(max_ny, h->g.ny);
     }
     double best = 1e300;
@@ -136,15 +132,13 @@ void build_plan(fdtd_batch* b, int K, int variant, int seg_req) {
     const int seg = seg_req > 0 ? seg_req : model_seg(b, K, variant);
     b->first_task.assign(n + 1, 0);
     b->n_strips.assign(n, 0);
-    b->slot_off.assign(n + 1, 0);
     b->max_ny = 0;
     b->max_P = 0;
     std::vector<int> task_sim;
     for (int s = 0; s < n; ++s) {
         fdtd_handle* h = b->hs[s];
         const int P = h->g.pml_cells;
-        const int min_seg = P + K + 1;
-        const std::vector<int> bounds = segment_bounds(h->g, std::max(seg, min_seg), min_seg);
+        const std::vector<int> bounds = segment_bounds(h->g, std::max(seg, K + 1), K);
         int* d = nullptr;
         BCK(cudaMalloc(&d, bounds.size() * sizeof(int)));
         BCK(cudaMemcpy(d, bounds.data(), bounds.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -154,7 +148,6 @@ void build_plan(fdtd_batch* b, int K, int variant, int seg_req) {
         b->n_strips[s] = strips;
         b->first_task[s + 1] = b->first_task[s] + tasks;
         task_sim.insert(task_sim.end(), tasks, s);
-        b->slot_off[s + 1] = b->slot_off[s] + (size_t)strips * 2 * std::max(P, 1) * 128;
         b->max_ny = std::max(b->max_ny, h->g.ny);
         b->max_P = std::max(b->max_P, P);
     }
@@ -163,8 +156,6 @@ void build_plan(fdtd_batch* b, int K, int variant, int seg_req) {
     BCK(cudaMemcpy(b->d_task_sim, task_sim.data(), task_sim.size() * sizeof(int), cudaMemcpyHostToDevice));
     BCK(cudaMalloc(&b->d_first_task, (n + 1) * sizeof(int)));
     BCK(cudaMemcpy(b->d_first_task, b->first_task.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice));
-    BCK(cudaMalloc(&b->d_slotE, std::max<size_t>(b->slot_off[n], 1) * sizeof(float)));
-    BCK(cudaMalloc(&b->d_slotH, std::max<size_t>(b->slot_off[n], 1) * sizeof(float)));
     BCK(cudaMalloc(&b->d_args, 2 * n * sizeof(BlockedArgs)));
     BCK(cudaMalloc(&b->d_twin, n * sizeof(TwinArgs)));
     b->pK = K;
@@ -192,8 +183,6 @@ void upload_args(fdtd_batch* b, bool dummy_dft) {
             a.ez_out = h->ez[o]; a.hx_out = h->hx[o]; a.hy_out = h->hy[o];
             a.psiE_in = h->psiE[c]; a.psiH_in = h->psiH[c];
             a.psiE_out = h->psiE[o]; a.psiH_out = h->psiH[o];
-            a.slotE = b->d_slotE + b->slot_off[s];
-            a.slotH = b->d_slotH + b->slot_off[s];
             a.seg_y0 = b->d_seg[s];
             a.n_strips = b->n_strips[s];
             a.n_tasks = b->first_task[s + 1] - b->first_task[s];

@@ -27,11 +27,13 @@
 // pairs columns q-1 and q (the neighbour lane's last label by shuffle).
 //
 // CPML rows (top/bottom P rows) carry their psi recursion from level to
-// level in a per-strip scratch area; the segment plan guarantees that only
-// the first and last segment of a strip ever touch CPML rows. The TF/SF
-// corrections (Sec. 2.5) are applied by every segment that computes row js;
-// DFT accumulation (Sec. 2.6) is done by the segment owning the monitor row,
-// which the plan keeps at least one row above its segment's end.
+// level in a per-warp shared-memory ring; any segment may hold CPML rows,
+// and only the segment owning a row stores its psi (like its fields). The
+// TF/SF corrections (Sec. 2.5) are applied by every segment that computes
+// row js; DFT accumulation (Sec. 2.6) is done by the segment owning the
+// monitor row, which the plan keeps at least one row above its segment's
+// end. Every segment but the first starts at row K or later, so its halo
+// rows exist.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -45,10 +47,6 @@ constexpr unsigned FULL = 0xffffffffu;
 
 __device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
     const float4 x = __ldg(reinterpret_cast<const float4*>(p));
-    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
-}
-__device__ __forceinline__ void ld4_rw(const float* p, float (&v)[4]) {
-    const float4 x = *reinterpret_cast<const float4*>(p);
     v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
 }
 __device__ __forceinline__ void st4(float* p, const float (&v)[4]) {
@@ -100,8 +98,8 @@ struct Lane {
 template <int K, bool GENERAL, int POL>
 __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[4],
                                         float (&fY)[4], uint32_t& fL, const int t,
-                                        const BlockedArgs& a, const Lane& ln, float* slotE,
-                                        float* slotH, const int64_t n0) {
+                                        const BlockedArgs& a, const Lane& ln, float4* ringE,
+                                        float4* ringH, const int64_t n0) {
     const float S = ln.S;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -133,7 +131,10 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
                 const float ik = a.s.pml_e[4 * ln.P + pe];
                 float psi[4];
                 if (k == 0) ld4(a.psiE_in + (size_t)pe * a.s.pitch + ln.gx, psi);
-                else ld4_rw(slotE + (size_t)pe * 128, psi);
+                else {
+                    const float4 v = ringE[(r % K) * 32];
+                    psi[0] = v.x; psi[1] = v.y; psi[2] = v.z; psi[3] = v.w;
+                }
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const float2 cc = POL ? make_float2(1.0f, S) : ln.coef[(cL >> (8 * q)) & 0xffu];
@@ -144,9 +145,10 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
                     oE[q] = ez_new_pml(cc.x, cc.y, p.E[k][q], dhy, dhx, ik, psi[q]);
                 }
                 if (k == K - 1) {
-                    if (ln.own) st4(a.psiE_out + (size_t)pe * a.s.pitch + ln.gx, psi);
+                    if (ln.own && r >= ln.y0 && r < ln.y1)
+                        st4(a.psiE_out + (size_t)pe * a.s.pitch + ln.gx, psi);
                 } else {
-                    st4(slotE + (size_t)pe * 128, psi);
+                    ringE[(r % K) * 32] = make_float4(psi[0], psi[1], psi[2], psi[3]);
                 }
             } else {
 #pragma unroll
@@ -166,7 +168,10 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
                     const float ik = a.s.pml_h[4 * ln.P + ph];
                     float psi[4];
                     if (k == 0) ld4(a.psiH_in + (size_t)ph * a.s.pitch + ln.gx, psi);
-                    else ld4_rw(slotH + (size_t)ph * 128, psi);
+                    else {
+                        const float4 v = ringH[(r % K) * 32];
+                        psi[0] = v.x; psi[1] = v.y; psi[2] = v.z; psi[3] = v.w;
+                    }
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         float d = __fsub_rn(oE[q], p.E[k + 1][q]);
@@ -180,9 +185,10 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
                         }
                     }
                     if (k == K - 1) {
-                        if (ln.own) st4(a.psiH_out + (size_t)ph * a.s.pitch + ln.gx, psi);
+                        if (ln.own && r >= ln.y0 && r < ln.y1)
+                            st4(a.psiH_out + (size_t)ph * a.s.pitch + ln.gx, psi);
                     } else {
-                        st4(slotH + (size_t)ph * 128, psi);
+                        ringH[(r % K) * 32] = make_float4(psi[0], psi[1], psi[2], psi[3]);
                     }
                 } else {
 #pragma unroll
@@ -279,8 +285,12 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float2*
     ln.own = (xl >= H) && (xl < H + a.w_int) && (xg_pre < ln.nx);
     ln.own_r = (a.s.jr >= ln.y0) && (a.s.jr < ln.y1);
     ln.own_t = (a.s.jt >= ln.y0) && (a.s.jt < ln.y1);
-    float* slotE = a.slotE + (size_t)strip * 2 * ln.P * 128 + xl;
-    float* slotH = a.slotH + (size_t)strip * 2 * ln.P * 128 + xl;
+    // CPML carries between levels: psi of a row is written by level k and
+    // read by level k+1 one iteration later, so K rows are in flight; a
+    // lane-private shared-memory ring indexed by row mod K holds them.
+    __shared__ float4 s_psi[2][K][32];
+    float4* ringE = &s_psi[0][0][lane];
+    float4* ringH = &s_psi[1][0][lane];
 
     Pipe<K> p;
 #pragma unroll
@@ -328,7 +338,7 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float2*
         __shared__ float4 ring[kRing][3][32];
         __shared__ uint32_t ring_l[kRing][32];
         auto issue = [&](const int row, const int slot) {
-            const bool ok = row < ny;
+            const bool ok = row >= 0 && row < ny;
             const size_t o = (size_t)(ok ? row : 0) * pitch + ln.gx;
             const int nb = ok ? 16 : 0;
             cp_async16(&ring[slot][0][lane], a.ez_in + o, nb);
@@ -352,8 +362,8 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float2*
             fY[0] = y4.x; fY[1] = y4.y; fY[2] = y4.z; fY[3] = y4.w;
             issue(t + kRing, slot);
             slot = (slot + 1 == kRing) ? 0 : slot + 1;
-            if (is_fast(t)) advance<K, false, POL>(p, fE, fX, fY, fL, t, a, ln, slotE, slotH, n0);
-            else advance<K, true, POL>(p, fE, fX, fY, fL, t, a, ln, slotE, slotH, n0);
+            if (is_fast(t)) advance<K, false, POL>(p, fE, fX, fY, fL, t, a, ln, ringE, ringH, n0);
+            else advance<K, true, POL>(p, fE, fX, fY, fL, t, a, ln, ringE, ringH, n0);
             finish(t, fE, fX, fY);
         }
         cp_async_wait<0>();
@@ -386,8 +396,8 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float2*
             for (int q = 0; q < 4; ++q) { nE[q] = 0.f; nX[q] = 0.f; nY[q] = 0.f; }
             nL = 0u;
         }
-        if (fast) advance<K, false, POL>(p, fE, fX, fY, fL, t, a, ln, slotE, slotH, n0);
-        else advance<K, true, POL>(p, fE, fX, fY, fL, t, a, ln, slotE, slotH, n0);
+        if (fast) advance<K, false, POL>(p, fE, fX, fY, fL, t, a, ln, ringE, ringH, n0);
+        else advance<K, true, POL>(p, fE, fX, fY, fL, t, a, ln, ringE, ringH, n0);
         finish(t, fE, fX, fY);
     };
     int t = t_begin;

@@ -49,7 +49,6 @@ struct BlockedArgs {
     float* ez_out; float* hx_out; float* hy_out;
     const float* psiE_in; const float* psiH_in;
     float* psiE_out; float* psiH_out;
-    float* slotE; float* slotH;   // per-strip CPML carries [n_strips][2][P][128]
     const int* seg_y0;
     int n_strips, n_tasks, w_int;
     int64_t n_base;               // batch launches: absolute step of the batch start
@@ -111,7 +110,7 @@ void compute_tables(fdtd_handle* h, int64_t upto);
 void upload_tables(fdtd_handle* h, int64_t upto);
 int sm_count(fdtd_handle* h);
 void sync_all(fdtd_handle* h);
-std::vector<int> segment_bounds(const fdtd_grid& g, int seg, int min_seg);
+std::vector<int> segment_bounds(const fdtd_grid& g, int seg, int K);
 BlockPlan& get_plan(fdtd_handle* h, int K);
 
 }  // namespace fdtd
@@ -155,8 +154,6 @@ struct fdtd_handle {
     double* d_flux = nullptr;
     double* h_flux = nullptr;  // pinned
     int* d_flag = nullptr;
-    float* slotE = nullptr; float* slotH = nullptr;
-    size_t slot_floats = 0;
     // incident-wave and phase tables (absolute step index)
     fdtd::IncidentGen gen;
     int64_t tab_cap = 0;

@@ -7,8 +7,8 @@
 // by its host framework, or a process whose device allocator belongs to
 // another runtime. fdtd_create/fdtd_run allocate (state, tables, plans), so
 // this entry point takes every input and output buffer from the caller and
-// keeps its own scratch (CPML carries, the segment table, the coefficient and
-// CPML tables, zeroed source tables and a sink for monitor sums) in one
+// keeps its own scratch (the segment table, the coefficient and CPML tables,
+// zeroed source tables and a sink for monitor sums) in one
 // file-scope __device__ array of kScratchBytes. Every GPU that loads the
 // library holds that array until the process exits.
 #include <cuda_runtime.h>
@@ -88,13 +88,11 @@ extern "C" int fdtd_blocked_advance_noalloc(const fdtd_grid* grid, const uint8_t
     const size_t tab_bytes = 8 * (2 * sizeof(float) + 2 * sizeof(double2));
     const size_t off_seg = align256(off_tab + tab_bytes);
     const size_t off_dft = align256(off_seg + (kMaxSegs + 1) * sizeof(int));
-    const size_t off_slot = align256(off_dft + (size_t)4 * g.nx * sizeof(double2));
-    const size_t slot_floats = (size_t)n_strips * 2 * (P > 0 ? P : 1) * 128;
-    const size_t need = off_slot + 2 * slot_floats * sizeof(float);
+    const size_t need = off_dft + (size_t)4 * g.nx * sizeof(double2);
     if (need > kScratchBytes) {
         std::snprintf(msg, sizeof msg,
                       "grid needs %zu bytes of scratch, more than the %zu-byte maximum "
-                      "(about nx * (pml_cells + 1) <= 300000)", need, kScratchBytes);
+                      "(about nx <= 130000)", need, kScratchBytes);
         return fail(err, err_len, FDTD_EINVAL, msg);
     }
 
@@ -210,8 +208,6 @@ extern "C" int fdtd_blocked_advance_noalloc(const fdtd_grid* grid, const uint8_t
     a.psiE_in = in[3]; a.psiH_in = in[4];
     a.ez_out = out[0]; a.hx_out = out[1]; a.hy_out = out[2];
     a.psiE_out = out[3]; a.psiH_out = out[4];
-    a.slotE = reinterpret_cast<float*>(sb + off_slot);
-    a.slotH = reinterpret_cast<float*>(sb + off_slot + slot_floats * sizeof(float));
     a.seg_y0 = reinterpret_cast<const int*>(sb + off_seg);
     a.n_strips = n_strips;
     a.n_tasks = n_strips * (nb - 1);
