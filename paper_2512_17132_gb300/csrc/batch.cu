@@ -97,7 +97,8 @@ void drop_plan(fdtd_batch* b) {
     b->planned = false;
 }
 
-// Wave model over the union of the batch: waves x (rows + 2K).
+// Wave model over the union of the batch: waves x (rows + 2K), each
+// simulation cut into ceil(ny / rows) segments so that no task is longer.
 int model_seg(fdtd_batch* b, int K, int variant) {
     int per_sm = blocked_warps_per_sm(K, variant, b->hs[0]->src.polarization);
     if (per_sm <= 0) per_sm = 8;
@@ -114,7 +115,7 @@ int model_seg(fdtd_batch* b, int K, int variant) {
         int64_t tasks = 0;
         for (auto* h : b->hs) {
             const int strips = (h->g.nx + w_int - 1) / w_int;
-            tasks += (int64_t)strips * std::max(1, h->g.ny / s);
+            tasks += (int64_t)strips * ((h->g.ny + s - 1) / s);   // no task longer than s rows
         }
         const int64_t waves = (tasks + W - 1) / W;
         const double cost = (double)waves * (s + 2.0 * K);
@@ -138,7 +139,10 @@ void build_plan(fdtd_batch* b, int K, int variant, int seg_req) {
     for (int s = 0; s < n; ++s) {
         fdtd_handle* h = b->hs[s];
         const int P = h->g.pml_cells;
-        const std::vector<int> bounds = segment_bounds(h->g, std::max(seg, K + 1), K);
+        // ceil(ny / seg) segments of at most seg rows (the wave model's count)
+        const int n_s = std::max(1, (h->g.ny + seg - 1) / seg);
+        const int seg_s = (h->g.ny + n_s - 1) / n_s;
+        const std::vector<int> bounds = segment_bounds(h->g, std::max(seg_s, K + 1), K);
         int* d = nullptr;
         BCK(cudaMalloc(&d, bounds.size() * sizeof(int)));
         BCK(cudaMemcpy(d, bounds.data(), bounds.size() * sizeof(int), cudaMemcpyHostToDevice));
