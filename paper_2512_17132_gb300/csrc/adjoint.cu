@@ -17,6 +17,9 @@
 //
 // Each reverse kernel recomputes the neighbour terms it needs instead of
 // staging them, so the adjoint of Ez and the CPML carries are ping-ponged.
+// Where rows split into float4s (nx % 4 == 0) the reverse kernels take four
+// columns per thread (k_adj_h4, k_adj_e4); the scalar kernels serve the
+// other widths; both give the same bits.
 //
 // in the library's units (Ez, eta0 H; ca, cb of Sec. 2.3). The monitor
 // sources follow from J = wR R + wT T with R, T the Poynting ratios of
@@ -67,6 +70,7 @@ struct AdjArgs {
     float* lX; float* lY;
     float* gA; float* gB;   // FP32 per-segment sums
     const float* tE; const float* tX; const float* tY; const float* tPE;   // tape state of step n
+    int n_coef;             // entries of coef (labelled handles)
 };
 
 __device__ __forceinline__ float2 cell_coef(const AdjArgs& a, int j, int i) {
@@ -199,6 +203,213 @@ __global__ void k_adj_e(AdjArgs a, int64_t n, const float* __restrict__ lE_in,
     lE_out[o] = __fmul_rn(cell_coef(a, j, i).x, eb);
 }
 
+// ---------------------------------------------------------------------------
+// Four columns per thread (nx % 4 == 0): the same per-cell expressions as
+// k_adj_h / k_adj_e, in the same order (bit-identical results), with float4
+// loads and stores and the label coefficients in shared memory, so that each
+// thread keeps four times the bytes in flight per load (the scalar kernels
+// are latency-bound on chains of dependent loads).
+
+__device__ __forceinline__ void ld4v(const float* p, float (&v)[4]) {
+    const float4 x = *reinterpret_cast<const float4*>(p);
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+}
+__device__ __forceinline__ void st4v(float* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+// coefficients (ca, cb) of cells (j, i0..i0+3)
+__device__ __forceinline__ void coef4(const AdjArgs& a, const float2* s_coef, int j, int i0,
+                                      float2 (&c)[4]) {
+    if (a.cellcoef) {
+        const float4* p = reinterpret_cast<const float4*>(a.cellcoef + (size_t)j * a.pitch + i0);
+        const float4 u = p[0], w = p[1];
+        c[0] = make_float2(u.x, u.y); c[1] = make_float2(u.z, u.w);
+        c[2] = make_float2(w.x, w.y); c[3] = make_float2(w.z, w.w);
+    } else {
+        const uint32_t L = *reinterpret_cast<const uint32_t*>(a.labels + (size_t)j * a.lpitch + i0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) c[q] = s_coef[(L >> (8 * q)) & 0xffu];
+    }
+}
+
+__device__ __forceinline__ float2 coef1(const AdjArgs& a, const float2* s_coef, int j, int i) {
+    const size_t o = (size_t)j * a.pitch + i;
+    return a.cellcoef ? a.cellcoef[o] : s_coef[a.labels[(size_t)j * a.lpitch + i]];
+}
+
+__device__ __forceinline__ void load_coef_table(const AdjArgs& a, float2* s_coef) {
+    if (!a.cellcoef)
+        for (int t = threadIdx.x; t < a.n_coef; t += blockDim.x) s_coef[t] = a.coef[t];
+    __syncthreads();
+}
+
+// adj_dez for columns i0..i0+3 of row j (mH_out row j written when given)
+__device__ __forceinline__ void adj_dez4(const AdjArgs& a, int j, int i0, int64_t n,
+                                         const float* mH_in, float* mH_out, float (&d)[4]) {
+    if (j <= 0 || j >= a.ny) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) d[q] = 0.f;
+        return;
+    }
+    const size_t o = (size_t)j * a.pitch + i0;
+    float x[4];
+    ld4v(a.lX + o, x);
+    if (j == a.jr || j == a.jr + 1 || j == a.jt || j == a.jt + 1)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) x[q] = __fadd_rn(x[q], src_h(a, j, i0 + q, n));
+    const int ph = pml_h_index(j, a.ny, a.P);
+    if (ph >= 0) {
+        const size_t qq = (size_t)ph * a.pitch + i0;
+        const float b = a.pml_h[ph], c = a.pml_h[2 * a.P + ph], ik = a.pml_h[4 * a.P + ph];
+        float m[4], mo[4];
+        ld4v(mH_in + qq, m);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float sx = __fmul_rn(a.S, x[q]);
+            const float nu = __fadd_rn(sx, m[q]);
+            mo[q] = __fmul_rn(b, nu);
+            d[q] = __fmaf_rn(c, nu, __fmul_rn(sx, ik));
+        }
+        if (mH_out) st4v(mH_out + qq, mo);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) d[q] = __fmul_rn(a.S, x[q]);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_adj_h4(AdjArgs a, int64_t n, const float* __restrict__ mH_in,
+                                                float* __restrict__ mH_out) {
+    const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int j = blockIdx.y;
+    if (i0 >= a.nx) return;
+    const size_t o = (size_t)j * a.pitch + i0;
+    float d0[4], d1[4], e[4], y[5];
+    adj_dez4(a, j, i0, n, mH_in, mH_out, d0);
+    adj_dez4(a, j + 1, i0, n, mH_in, nullptr, d1);
+    ld4v(a.lE + o, e);
+    ld4v(a.lY + o, *reinterpret_cast<float (*)[4]>(y));
+    y[4] = a.lY[(size_t)j * a.pitch + ((i0 + 4 == a.nx) ? 0 : i0 + 4)];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        e[q] = __fadd_rn(e[q], __fmul_rn(a.S, __fsub_rn(y[q], y[q + 1])));
+        e[q] = __fadd_rn(e[q], __fsub_rn(d0[q], d1[q]));
+        if (j == a.jr || j == a.jt) e[q] = __fadd_rn(e[q], src_e(a, j, i0 + q, n));
+    }
+    st4v(a.lE + o, e);
+}
+
+// cbar and ghx (adj_curl) of cells (j, i0..i0+3); mE_out row j written when given
+__device__ __forceinline__ void adj_curl4(const AdjArgs& a, const float2* s_coef, int j, int i0,
+                                          const float* lE_in, const float* mE_in, float* mE_out,
+                                          float (&cbar)[4], float (&ghx)[4]) {
+    float2 c[4];
+    coef4(a, s_coef, j, i0, c);
+    float eb[4];
+    ld4v(lE_in + (size_t)j * a.pitch + i0, eb);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) cbar[q] = __fmul_rn(c[q].y, eb[q]);
+    const int pe = pml_e_index(j, a.ny, a.P);
+    if (pe >= 0) {
+        const size_t qq = (size_t)pe * a.pitch + i0;
+        const float b = a.pml_e[pe], cc = a.pml_e[2 * a.P + pe], ik = a.pml_e[4 * a.P + pe];
+        float m[4], mo[4];
+        ld4v(mE_in + qq, m);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float rho = __fadd_rn(cbar[q], m[q]);
+            mo[q] = __fmul_rn(b, rho);
+            ghx[q] = __fmaf_rn(cc, rho, __fmul_rn(cbar[q], ik));
+        }
+        if (mE_out) st4v(mE_out + qq, mo);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ghx[q] = cbar[q];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_adj_e4(AdjArgs a, int64_t n, const float* __restrict__ lE_in,
+                                                float* __restrict__ lE_out,
+                                                const float* __restrict__ mE_in,
+                                                float* __restrict__ mE_out) {
+    __shared__ float2 s_coef[256];
+    load_coef_table(a, s_coef);
+    const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int j = blockIdx.y;
+    if (i0 >= a.nx) return;
+    const size_t o = (size_t)j * a.pitch + i0;
+    const int ir = (i0 + 4 == a.nx) ? 0 : i0 + 4;
+    const int il = (i0 == 0) ? a.nx - 1 : i0 - 1;
+    float eb[4];
+    ld4v(lE_in + o, eb);
+    // forward curl of step n from the taped state (same rounding as forward)
+    float ty[5], x0[4], x1[4], te[4], curl[4];
+    ld4v(a.tY + o, *reinterpret_cast<float (*)[4]>(ty));
+    ty[4] = a.tY[(size_t)j * a.pitch + ir];
+    ld4v(a.tX + o, x0);
+    if (j + 1 < a.ny) {
+        ld4v(a.tX + o + a.pitch, x1);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) x1[q] = 0.0f;
+    }
+    ld4v(a.tE + o, te);
+    const int pe = pml_e_index(j, a.ny, a.P);
+    float psi_old[4];
+    if (pe >= 0) ld4v(a.tPE + (size_t)pe * a.pitch + i0, psi_old);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float dhy = __fsub_rn(ty[q + 1], ty[q]);
+        float dhx = __fsub_rn(x1[q], x0[q]);
+        if (j == a.js) dhx = __fsub_rn(dhx, a.hinc[n]);
+        if (pe >= 0) {
+            const float b = a.pml_e[pe], cc = a.pml_e[2 * a.P + pe], ik = a.pml_e[4 * a.P + pe];
+            const float psi = psi_new(b, cc, psi_old[q], dhx);
+            curl[q] = __fadd_rn(dhy, __fmaf_rn(dhx, ik, psi));
+        } else {
+            curl[q] = __fadd_rn(dhy, dhx);
+        }
+    }
+    float gA[4], gB[4];
+    ld4v(a.gA + o, gA);
+    ld4v(a.gB + o, gB);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        gA[q] = __fmaf_rn(eb[q], te[q], gA[q]);
+        gB[q] = __fmaf_rn(eb[q], curl[q], gB[q]);
+    }
+    st4v(a.gA + o, gA);
+    st4v(a.gB + o, gB);
+    float c0[4], g0[4], gu[4];
+    adj_curl4(a, s_coef, j, i0, lE_in, mE_in, mE_out, c0, g0);
+    const float cl0 = __fmul_rn(coef1(a, s_coef, j, il).y, lE_in[(size_t)j * a.pitch + il]);
+    if (j > 0) {
+        float dummy[4];
+        adj_curl4(a, s_coef, j - 1, i0, lE_in, mE_in, nullptr, dummy, gu);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) gu[q] = 0.f;
+    }
+    float ly[4], lx[4], leo[4];
+    ld4v(a.lY + o, ly);
+    ld4v(a.lX + o, lx);
+    const bool mon = (j == a.jr || j == a.jr + 1 || j == a.jt || j == a.jt + 1);
+    float2 cc[4];
+    coef4(a, s_coef, j, i0, cc);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float cl = q ? c0[q - 1] : cl0;
+        ly[q] = __fadd_rn(ly[q], __fsub_rn(cl, c0[q]));
+        float x = lx[q];
+        if (mon) x = __fadd_rn(x, src_h(a, j, i0 + q, n));
+        lx[q] = __fadd_rn(x, __fsub_rn(gu[q], g0[q]));
+        leo[q] = __fmul_rn(cc[q].x, eb[q]);
+    }
+    st4v(a.lY + o, ly);
+    st4v(a.lX + o, lx);
+    st4v(lE_out + o, leo);
+}
+
 __global__ void k_adj_flush(float* gA, float* gB, double* GA, double* GB, int nx, int ny,
                             int pitch) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -312,7 +523,7 @@ void step_out_of_place(fdtd_handle* h, const StateView& in, const StateView& out
             b.n_strips = pl->n_strips;
             b.n_tasks = pl->n_strips * pl->n_segs;
             b.w_int = pl->w_int;
-            launch_blocked(b, 1, 0, n, h->stream);
+            launch_blocked(b, 1, h->opt_variant, n, h->stream);
             return;
         }
     }
@@ -434,6 +645,10 @@ int fdtd_backward(fdtd_handle* h, double wR, double wT, double* g_eps, double* g
         double* GA = dbl;
         double* GB = dbl + f;
         const dim3 blk(256), grd((nx + 255) / 256, ny);
+        // four columns per thread where rows split into float4s
+        const bool vec4 = (nx % 4 == 0);
+        const dim3 grd4((nx / 4 + 255) / 256, ny);
+        a.n_coef = h->n_labels;
         const int64_t n_seg = (steps + every - 1) / every;
         for (int64_t c = n_seg - 1; c >= 0; --c) {
             const int64_t c0 = c * every;
@@ -447,10 +662,17 @@ int fdtd_backward(fdtd_handle* h, double wR, double wT, double* g_eps, double* g
                 const StateView v = view(h, tape[m]);
                 a.tE = v.E; a.tX = v.X; a.tY = v.Y; a.tPE = v.PE;
                 a.lE = lEb[le_cur];
-                k_adj_h<<<grd, blk, 0, h->stream>>>(a, n, mHb[ph_cur], mHb[ph_cur ^ 1]);
-                ph_cur ^= 1;
-                k_adj_e<<<grd, blk, 0, h->stream>>>(a, n, lEb[le_cur], lEb[le_cur ^ 1],
-                                                    mEb[pe_cur], mEb[pe_cur ^ 1]);
+                if (vec4) {
+                    k_adj_h4<<<grd4, blk, 0, h->stream>>>(a, n, mHb[ph_cur], mHb[ph_cur ^ 1]);
+                    ph_cur ^= 1;
+                    k_adj_e4<<<grd4, blk, 0, h->stream>>>(a, n, lEb[le_cur], lEb[le_cur ^ 1],
+                                                          mEb[pe_cur], mEb[pe_cur ^ 1]);
+                } else {
+                    k_adj_h<<<grd, blk, 0, h->stream>>>(a, n, mHb[ph_cur], mHb[ph_cur ^ 1]);
+                    ph_cur ^= 1;
+                    k_adj_e<<<grd, blk, 0, h->stream>>>(a, n, lEb[le_cur], lEb[le_cur ^ 1],
+                                                        mEb[pe_cur], mEb[pe_cur ^ 1]);
+                }
                 pe_cur ^= 1;
                 le_cur ^= 1;
             }
