@@ -535,6 +535,32 @@ void step_out_of_place(fdtd_handle* h, const StateView& in, const StateView& out
     launch_naive_step(s, out.E, out.X, out.Y, out.PE, out.PH, n, h->stream);
 }
 
+// Recompute K steps n..n+K-1 from state `in` in one blocked launch (code
+// shape 4): the launch writes the final state to `out` and the states after
+// the intermediate steps to tape_ptrs[0..K-2] (device array of state base
+// pointers); the same arithmetic as K one-step launches, so the same bits.
+void steps_to_tape(fdtd_handle* h, const StateView& in, const StateView& out, int K, int64_t n,
+                   float* const* tape_ptrs, double2* dummy) {
+    StepArgs s = step_args(h);
+    s.dft = dummy;
+    const int keep = h->opt_seg;
+    h->opt_seg = 0;
+    BlockPlan& pl = get_plan(h, K);
+    h->opt_seg = keep;
+    BlockedArgs b{};
+    b.s = s;
+    b.ez_in = in.E; b.hx_in = in.X; b.hy_in = in.Y;
+    b.ez_out = out.E; b.hx_out = out.X; b.hy_out = out.Y;
+    b.psiE_in = in.PE; b.psiH_in = in.PH; b.psiE_out = out.PE; b.psiH_out = out.PH;
+    b.seg_y0 = pl.d_seg_y0;
+    b.n_strips = pl.n_strips;
+    b.n_tasks = pl.n_strips * pl.n_segs;
+    b.w_int = pl.w_int;
+    b.tape = tape_ptrs;
+    b.tape_f = (size_t)h->pitch * h->g.ny;
+    launch_blocked(b, K, 4, n, h->stream);
+}
+
 }  // namespace
 
 extern "C" {
@@ -584,7 +610,9 @@ int fdtd_backward(fdtd_handle* h, double wR, double wT, double* g_eps, double* g
     float* buf = nullptr;
     double* dbl = nullptr;
     double2* dummy = nullptr;
+    float** d_tape_ptrs = nullptr;
     auto cleanup = [&]() {
+        if (d_tape_ptrs) cudaFree(d_tape_ptrs);
         for (auto& t : tape) cudaFree(t);
         if (buf) cudaFree(buf);
         if (dbl) cudaFree(dbl);
@@ -623,6 +651,14 @@ int fdtd_backward(fdtd_handle* h, double wR, double wT, double* g_eps, double* g
         const size_t sf = state_floats(h);
         tape.assign((size_t)std::min<int64_t>(every, steps), nullptr);
         for (auto& t : tape) ACK(cudaMalloc(&t, sf * sizeof(float)));
+        // multi-step recompute (labelled grids with nx % 4 == 0): a device
+        // array of the tape states' base pointers
+        const bool multi = !h->maps && nx % 4 == 0;
+        if (multi) {
+            ACK(cudaMalloc(&d_tape_ptrs, tape.size() * sizeof(float*)));
+            ACK(cudaMemcpy(d_tape_ptrs, tape.data(), tape.size() * sizeof(float*),
+                           cudaMemcpyHostToDevice));
+        }
         // lE[2] lX lY gA gB (f each) + mE[2] mH[2] (pr each)
         ACK(cudaMalloc(&buf, (6 * f + 4 * pr) * sizeof(float)));
         ACK(cudaMemsetAsync(buf, 0, (6 * f + 4 * pr) * sizeof(float), h->stream));
@@ -655,8 +691,19 @@ int fdtd_backward(fdtd_handle* h, double wR, double wT, double* g_eps, double* g
             const int L = (int)std::min<int64_t>(every, steps - c0);
             ACK(cudaMemcpyAsync(tape[0], h->ck[(size_t)c], sf * sizeof(float),
                                 cudaMemcpyDeviceToDevice, h->stream));
-            for (int m = 0; m + 1 < L; ++m)
-                step_out_of_place(h, view(h, tape[m]), view(h, tape[m + 1]), c0 + m, dummy);
+            if (multi) {
+                const int Kmax = std::min(std::max(h->opt_block, 1), blocked_max_K());
+                for (int m = 0; m + 1 < L;) {
+                    const int Kr = std::min(Kmax, L - 1 - m);
+                    steps_to_tape(h, view(h, tape[m]), view(h, tape[m + Kr]), Kr, c0 + m,
+                                  d_tape_ptrs + m + 1, dummy);
+                    h->total_launches += 1;
+                    m += Kr;
+                }
+            } else {
+                for (int m = 0; m + 1 < L; ++m)
+                    step_out_of_place(h, view(h, tape[m]), view(h, tape[m + 1]), c0 + m, dummy);
+            }
             for (int m = L - 1; m >= 0; --m) {
                 const int64_t n = c0 + m;
                 const StateView v = view(h, tape[m]);

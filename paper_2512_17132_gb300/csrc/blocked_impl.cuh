@@ -95,7 +95,7 @@ struct Lane {
 // GENERAL = false is the lean path for iterations whose K rows hold no
 // CPML, source, monitor or boundary row and lie inside the valid range;
 // both paths round identically.
-template <int K, bool GENERAL, int POL>
+template <int K, bool GENERAL, int POL, int V>
 __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[4],
                                         float (&fY)[4], uint32_t& fL, const int t,
                                         const BlockedArgs& a, const Lane& ln, float4* ringE,
@@ -149,6 +149,8 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
                         st4(a.psiE_out + (size_t)pe * a.s.pitch + ln.gx, psi);
                 } else {
                     ringE[(r % K) * 32] = make_float4(psi[0], psi[1], psi[2], psi[3]);
+                    if (V == 4 && ln.own && r >= ln.y0 && r < ln.y1)
+                        st4(a.tape[k] + 3 * a.tape_f + (size_t)pe * a.s.pitch + ln.gx, psi);
                 }
             } else {
 #pragma unroll
@@ -218,6 +220,13 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
                     oY[q] = h_new(p.Y[k][q], S, dy);
                 }
             }
+            if (V == 4 && k + 1 < K && ln.own && r >= ln.y0 && r < ln.y1) {
+                // code shape 4: the state after step k+1 of this row
+                float* t = a.tape[k] + (size_t)r * a.s.pitch + ln.gx;
+                st4(t, oE);
+                st4(t + a.tape_f, oX);
+                st4(t + 2 * a.tape_f, oY);
+            }
             if (GENERAL && ln.own) {
                 if (ln.own_r && r == a.s.jr) {
                     const double2 ph = a.s.phE[n];
@@ -264,7 +273,9 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
 // Code shapes V: 0 one row per loop trip with a one-row register prefetch;
 // 1 two rows per loop trip on plain stretches; 2 level-0 rows streamed
 // through a shared-memory ring filled kRing rows ahead by cp.async; 3 the
-// same code as 2 (built under a register cap, see k_blocked_cap).
+// same code as 2 (built under a register cap, see k_blocked_cap); 4 shape 2
+// that also stores the state after every intermediate step of the launch
+// (its owned rows) into BlockedArgs::tape, for the adjoint's recompute.
 template <int K, int V, int POL>
 __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float2* s_coef,
                                              const int task, const int64_t n0) {
@@ -362,8 +373,8 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float2*
             fY[0] = y4.x; fY[1] = y4.y; fY[2] = y4.z; fY[3] = y4.w;
             issue(t + kRing, slot);
             slot = (slot + 1 == kRing) ? 0 : slot + 1;
-            if (is_fast(t)) advance<K, false, POL>(p, fE, fX, fY, fL, t, a, ln, ringE, ringH, n0);
-            else advance<K, true, POL>(p, fE, fX, fY, fL, t, a, ln, ringE, ringH, n0);
+            if (is_fast(t)) advance<K, false, POL, V>(p, fE, fX, fY, fL, t, a, ln, ringE, ringH, n0);
+            else advance<K, true, POL, V>(p, fE, fX, fY, fL, t, a, ln, ringE, ringH, n0);
             finish(t, fE, fX, fY);
         }
         cp_async_wait<0>();
@@ -396,8 +407,8 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float2*
             for (int q = 0; q < 4; ++q) { nE[q] = 0.f; nX[q] = 0.f; nY[q] = 0.f; }
             nL = 0u;
         }
-        if (fast) advance<K, false, POL>(p, fE, fX, fY, fL, t, a, ln, ringE, ringH, n0);
-        else advance<K, true, POL>(p, fE, fX, fY, fL, t, a, ln, ringE, ringH, n0);
+        if (fast) advance<K, false, POL, V>(p, fE, fX, fY, fL, t, a, ln, ringE, ringH, n0);
+        else advance<K, true, POL, V>(p, fE, fX, fY, fL, t, a, ln, ringE, ringH, n0);
         finish(t, fE, fX, fY);
     };
     int t = t_begin;

@@ -52,6 +52,11 @@ struct BlockedArgs {
     const int* seg_y0;
     int n_strips, n_tasks, w_int;
     int64_t n_base;               // batch launches: absolute step of the batch start
+    // code shape 4 (adjoint recompute): states after each of steps 1..K-1 of
+    // the launch, as base pointers of [Ez | Hx | Hy | psi_E] blocks of
+    // tape_f, tape_f, tape_f floats and 2P rows
+    float* const* tape;
+    size_t tape_f;
 };
 
 // Arguments of the batched blocked kernel (all simulations in one launch).
