@@ -176,13 +176,30 @@ def _barrier(world):
 
 
 def _max_over_ranks(world, v):
+    """The largest value over the ranks (the slowest rank sets the job time);
+    a CUDA tensor under NCCL, a host tensor under gloo."""
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def rank_order(rank, steps, warmup):
+    """Wavelengths of a rank's warm-up and timed runs: each rank starts at its
+    own place in the cycle, so the ranks' runs are independent problems
+    (weak scaling, no data exchanged)."""
+    return [WAVELENGTHS[(rank * (steps + warmup) + i) % len(WAVELENGTHS)]
+            for i in range(warmup + steps)]
+
+
+def aggregate_rate(world, steps, cells_per_run, elapsed_max):
+    """Whole-job throughput in Gcell-updates/s: all ranks' runs over the
+    slowest rank's time."""
+    return world * steps * cells_per_run / elapsed_max / 1e9
 
 
 # -- CPU baseline (the FP64 oracle) -------------------------------------------
@@ -489,7 +506,7 @@ def main():
     fdtd.load_library()
 
     K, W = args.steps, args.warmup
-    order = [WAVELENGTHS[(rank * (K + W) + i) % len(WAVELENGTHS)] for i in range(W + K)]
+    order = rank_order(rank, K, W)
     specs = {lam: workload(args, lam) for lam in set(order)}
     spec0 = specs[order[-1]]
     cells_per_run = spec0.nx * spec0.ny * spec0.steps
@@ -522,7 +539,7 @@ def main():
     clk = clocks.stop() if clocks else None
     after = {lam: s.stats() for lam, s in sims.items()}
     elapsed = _max_over_ranks(world, elapsed)
-    value = world * K * cells_per_run / elapsed / 1e9
+    value = aggregate_rate(world, K, cells_per_run, elapsed)
 
     st_ms = sum(after[l]["stencil_ms"] - before[l]["stencil_ms"] for l in sims)
     st_n = sum(after[l]["stencil_launches"] - before[l]["stencil_launches"] for l in sims)

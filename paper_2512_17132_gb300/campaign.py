@@ -105,8 +105,31 @@ def _assemble(R, T, wavelengths, n_slices, pols, widths):
                 T_pol=T_pol, R=Rm, T=Tm, A=1.0 - Rm - Tm, widths=widths, pols=tuple(pols))
 
 
+def shard(n_runs, rank, world):
+    """Indices of the runs a rank takes (round-robin): the runs of a
+    campaign are independent problems, so ranks share nothing but the final
+    R and T scalars."""
+    return list(range(rank, n_runs, world))
+
+
+def gather_runs(n_runs, idx, R_loc, T_loc, world):
+    """R and T of all runs on every rank, from each rank's share: one sum
+    over the ranks of arrays that hold a rank's values at its own indices
+    (host tensors under gloo, device tensors under NCCL)."""
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.zeros((2, n_runs), dtype=torch.float64)
+    t[0, idx] = torch.as_tensor(np.asarray(R_loc, dtype=np.float64))
+    t[1, idx] = torch.as_tensor(np.asarray(T_loc, dtype=np.float64))
+    t = t.to(dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    t = t.cpu().numpy()
+    return t[0], t[1]
+
+
 def run_campaign(make_spec, wavelengths, n_slices=5, pols=(fdtd.FDTD_POL_S, fdtd.FDTD_POL_P),
-                 steps=None, runner=None, chunk=64):
+                 steps=None, runner=None, chunk=64, rank=0, world=1):
     """Spectrum of a cross-section the way Sec. 4 builds it: for every
     wavelength, every slice and every polarisation one independent run; the
     slices are averaged (weighted by width, the plain mean for equal strips)
@@ -117,11 +140,18 @@ def run_campaign(make_spec, wavelengths, n_slices=5, pols=(fdtd.FDTD_POL_S, fdtd
     the default is run_sweep (batched, one batch per polarisation). Returns
     a dict: wavelengths; R_runs, T_runs of shape (n_lambda, n_slices, n_pols);
     R_pol, T_pol (n_lambda, n_pols) slice-averaged; R, T, A (n_lambda)
-    averaged over the polarisations; widths."""
+    averaged over the polarisations; widths. With world > 1 (one process
+    per GPU, torch.distributed initialised) each rank runs its round-robin
+    share of the runs and every rank returns the whole campaign."""
     runner = runner or (lambda specs, st: run_sweep(specs, steps=st, chunk=chunk))
     wl = list(wavelengths)
     specs, widths = _plan(make_spec, wl, n_slices, pols)
-    R, T = runner(specs, steps)
+    if world > 1:
+        idx = shard(len(specs), rank, world)
+        R_loc, T_loc = runner([specs[i] for i in idx], steps) if idx else ([], [])
+        R, T = gather_runs(len(specs), idx, R_loc, T_loc, world)
+    else:
+        R, T = runner(specs, steps)
     return _assemble(R, T, wl, n_slices, pols, widths)
 
 
