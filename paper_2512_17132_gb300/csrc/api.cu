@@ -5,6 +5,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <tuple>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -85,8 +87,8 @@ StepArgs step_args(fdtd_handle* h) {
 
 // Grow the incident/phase tables so that steps [0, n_end) can be produced.
 void ensure_tables(fdtd_handle* h, int64_t n_end) {
-    if (n_end <= h->gen.plan_end) return;
-    int64_t plan = h->gen.plan_end > 0 ? std::max(n_end, 2 * h->gen.plan_end) : n_end;
+    if (n_end <= h->tab_plan) return;
+    int64_t plan = h->tab_plan > 0 ? std::max(n_end, 2 * h->tab_plan) : n_end;
     if (plan > h->tab_cap) {
         CK(cudaStreamSynchronize(h->stream));
         CK(cudaStreamSynchronize(h->twin_stream));
@@ -116,23 +118,57 @@ void ensure_tables(fdtd_handle* h, int64_t n_end) {
         h->h_hinc = hh; h->h_einc = he; h->h_phE = hpe; h->h_phH = hph;
         h->tab_cap = cap;
     }
-    h->gen.reset(plan);
+    h->tab_plan = plan;
 }
 
 // Host part: compute incident and phase table entries up to step `upto`
 // into the pinned buffers (no CUDA calls; handles may run in parallel).
 void compute_tables(fdtd_handle* h, int64_t upto) {
-    while (h->gen.m < upto) {
-        const int64_t m = h->gen.m;
-        float hv, ev;
-        h->gen.step(&hv, &ev);
-        h->h_hinc[m] = hv;
-        h->h_einc[m] = ev;
-        const double aE = h->omega * ((double)m + 0.5) * h->g.dt;
-        const double aH = h->omega * ((double)m + 1.0) * h->g.dt;
-        h->h_phE[m] = make_double2(std::cos(aE), std::sin(aE));
-        h->h_phH[m] = make_double2(std::cos(aH), std::sin(aH));
+    if (h->tab_m >= upto) return;
+    TableStore& st = *h->tables;
+    std::lock_guard<std::mutex> lk(st.mu);
+    const int64_t have = (int64_t)st.hinc.size();
+    if (have < upto) {
+        if (upto > st.gen.plan_end) {
+            // a longer plan: restart the generator and run it up to the
+            // values already stored (they stay valid), then extend them
+            st.gen.reset(std::max(h->tab_plan, 2 * st.gen.plan_end));
+            float hv, ev;
+            while (st.gen.m < have) st.gen.step(&hv, &ev);
+        }
+        st.hinc.resize(upto); st.einc.resize(upto);
+        st.phE.resize(upto); st.phH.resize(upto);
+        while (st.gen.m < upto) {
+            const int64_t m = st.gen.m;
+            st.gen.step(&st.hinc[m], &st.einc[m]);
+            const double aE = st.omega * ((double)m + 0.5) * st.gen.dt;
+            const double aH = st.omega * ((double)m + 1.0) * st.gen.dt;
+            st.phE[m] = make_double2(std::cos(aE), std::sin(aE));
+            st.phH[m] = make_double2(std::cos(aH), std::sin(aH));
+        }
     }
+    const int64_t m0 = h->tab_m;
+    std::copy(st.hinc.begin() + m0, st.hinc.begin() + upto, h->h_hinc + m0);
+    std::copy(st.einc.begin() + m0, st.einc.begin() + upto, h->h_einc + m0);
+    std::copy(st.phE.begin() + m0, st.phE.begin() + upto, h->h_phE + m0);
+    std::copy(st.phH.begin() + m0, st.phH.begin() + upto, h->h_phH + m0);
+    h->tab_m = upto;
+}
+
+std::shared_ptr<TableStore> table_store(const IncidentGen& p, double omega) {
+    using Key = std::tuple<int, double, double, double, double, double>;
+    static std::mutex mu;
+    static std::map<Key, std::weak_ptr<TableStore>> reg;
+    const Key key{p.kind, p.S, p.dt, p.lambda0, p.bw, p.t0_over_tau};
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto it = reg.begin(); it != reg.end();) it = it->second.expired() ? reg.erase(it) : ++it;
+    if (auto sp = reg[key].lock()) return sp;
+    auto sp = std::make_shared<TableStore>();
+    sp->gen = p;
+    sp->gen.reset(0);
+    sp->omega = omega;
+    reg[key] = sp;
+    return sp;
 }
 
 // Queue the upload of the computed entries not yet on the device.
@@ -658,10 +694,11 @@ static int create_impl(const fdtd_grid* grid, const uint8_t* labels, const fdtd_
             CK(cudaMemcpy(h->cell_sig, hs.data(), cells * sizeof(double), cudaMemcpyHostToDevice));
         }
 
-        IncidentGen& gen = h->gen;
+        IncidentGen gen;
         gen.S = h->S; gen.dt = g.dt; gen.lambda0 = source->lambda0;
         gen.bw = source->rel_bandwidth; gen.t0_over_tau = source->t0_over_tau;
         gen.kind = source->kind;
+        h->tables = table_store(gen, h->omega);
         CK(cudaStreamSynchronize(h->stream));
         *out = h;
         return FDTD_OK;

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -30,6 +32,21 @@ struct IncidentGen {
     double source(double t) const;
     void step(float* hinc, float* einc);
 };
+
+// Incident and DFT-phase tables shared by all handles with the same source,
+// Courant number and time step (e.g. the slices and polarisations of one
+// wavelength in a campaign): computed once, copied into each handle's
+// pinned buffers. Values are exact for every step below gen.plan_end, so a
+// store grown for a longer run serves shorter ones bit for bit. A store lives
+// while a handle holds it.
+struct TableStore {
+    std::mutex mu;
+    IncidentGen gen;                  // next step to produce: gen.m
+    double omega = 0;
+    std::vector<float> hinc, einc;    // steps [0, hinc.size())
+    std::vector<double2> phE, phH;
+};
+std::shared_ptr<TableStore> table_store(const IncidentGen& params, double omega);
 
 // Segment plan of the temporally blocked kernel for one block depth.
 struct BlockPlan {
@@ -160,7 +177,9 @@ struct fdtd_handle {
     double* h_flux = nullptr;  // pinned
     int* d_flag = nullptr;
     // incident-wave and phase tables (absolute step index)
-    fdtd::IncidentGen gen;
+    std::shared_ptr<fdtd::TableStore> tables;
+    int64_t tab_plan = 0;       // steps the buffers are planned for
+    int64_t tab_m = 0;          // entries [0, tab_m) are in the pinned buffers
     int64_t tab_cap = 0;
     float* d_hinc = nullptr; float* d_einc = nullptr;
     double2* d_phE = nullptr; double2* d_phH = nullptr;
