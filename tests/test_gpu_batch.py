@@ -124,3 +124,24 @@ def test_batch_rejects_bad_members(fd):
         assert "nx % 4" in str(e.value)
         with pytest.raises(fd.FDTDError):
             fd.fdtd_batch_create([c.h, c.h])
+
+
+def test_shared_incident_tables_give_identical_runs(fd):
+    # handles with the same source share one table store; a run that goes
+    # past the store's plan regrows it. Interleaved handles must give the
+    # bits of a handle run alone.
+    from fdtd_inputs import config_c1b
+    spec = config_c1b(nx=64, steps=1)
+    with fd.Simulation(spec) as ref:
+        ref.run(2600)
+        want = ref.flux_raw()
+        want_f = ref.fields()
+    with fd.Simulation(spec) as a:
+        a.run(300)                          # store planned for 300 steps
+        with fd.Simulation(spec) as b:
+            b.run(2600)                     # regrows the shared store
+            np.testing.assert_array_equal(b.flux_raw(), want)
+        a.run(2300)                         # continues from the regrown store
+        np.testing.assert_array_equal(a.flux_raw(), want)
+        for x, y in zip(a.fields(), want_f):
+            assert np.array_equal(x, y)
