@@ -133,8 +133,9 @@ typedef struct fdtd_stats {
 #define FDTD_OPT_WATCHDOG 5    /* check fields for non-finite values every N steps (0 off) */
 #define FDTD_OPT_VARIANT 6     /* blocked-kernel code shape: 0 one row per loop trip with a register
                                   prefetch, 1 two rows per trip, 2 rows streamed through a
-                                  shared-memory ring by cp.async (default), 3 shape 2 built
-                                  under a 224-register cap; P handles run shapes 2 and 3 */
+                                  shared-memory ring by cp.async, two lean rows per trip
+                                  (default), 3 the ring with one row per trip, built under a
+                                  224-register cap; P handles run shapes 2 and 3 */
 #define FDTD_OPT_GRAPH 7       /* batches: replay captured CUDA graphs of launch chunks (default 1) */
 
 /* Create a simulation. grid, labels (ny*nx uint8, values < n_labels), table

@@ -272,8 +272,9 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
 // One warp task: strip `task % n_strips` of segment `task / n_strips`.
 // Code shapes V: 0 one row per loop trip with a one-row register prefetch;
 // 1 two rows per loop trip on plain stretches; 2 level-0 rows streamed
-// through a shared-memory ring filled kRing rows ahead by cp.async; 3 the
-// same code as 2 (built under a register cap, see k_blocked_cap); 4 shape 2
+// through a shared-memory ring filled kRing rows ahead by cp.async, two rows
+// per loop trip on lean stretches; 3 the ring with one row per trip (built
+// under a register cap, see k_blocked_cap); 4 the ring, one row per trip,
 // that also stores the state after every intermediate step of the launch
 // (its owned rows) into BlockedArgs::tape, for the adjoint's recompute.
 template <int K, int V, int POL>
@@ -362,8 +363,7 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float2*
 #pragma unroll
         for (int d = 0; d < kRing; ++d) issue(t_begin + d, d);
         int slot = 0;
-#pragma unroll 1
-        for (int t = t_begin; t < t_end; ++t) {
+        auto row = [&](const int t, const bool fast) {
             cp_async_wait<kRing - 1>();
             float fE[4], fX[4], fY[4];
             const float4 e4 = ring[slot][0][lane], x4 = ring[slot][1][lane], y4 = ring[slot][2][lane];
@@ -373,9 +373,24 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float2*
             fY[0] = y4.x; fY[1] = y4.y; fY[2] = y4.z; fY[3] = y4.w;
             issue(t + kRing, slot);
             slot = (slot + 1 == kRing) ? 0 : slot + 1;
-            if (is_fast(t)) advance<K, false, POL, V>(p, fE, fX, fY, fL, t, a, ln, ringE, ringH, n0);
+            if (fast) advance<K, false, POL, V>(p, fE, fX, fY, fL, t, a, ln, ringE, ringH, n0);
             else advance<K, true, POL, V>(p, fE, fX, fY, fL, t, a, ln, ringE, ringH, n0);
             finish(t, fE, fX, fY);
+        };
+        // Two lean rows per loop trip: every pipeline register is replaced
+        // each row while its old value is still being read, so a one-row
+        // loop copies the new values back at the end of each trip; over two
+        // rows the two register sets alternate and the copies disappear.
+#pragma unroll 1
+        for (int t = t_begin; t < t_end;) {
+            if (V == 2 && t + 1 < t_end && is_fast(t) && is_fast(t + 1)) {
+                row(t, true);
+                row(t + 1, true);
+                t += 2;
+            } else {
+                row(t, is_fast(t));
+                t += 1;
+            }
         }
         cp_async_wait<0>();
         return;
@@ -441,10 +456,10 @@ __global__ void __launch_bounds__(32) k_blocked(const BlockedArgs a, const int64
     blocked_kernel_body<K, V, POL>(a, n0);
 }
 
-// Code shape 3: shape 2 compiled under a 224-register cap (8 one-warp
-// blocks per SM, as the uncapped build). With equal-height segments it was
-// 1-2 % faster than shape 2; with the cost-balanced segment plan shape 2 at
-// K = 8 is faster, and shape 3 stays available as an option.
+// Code shape 3: the ring with one row per loop trip, compiled under a
+// 224-register cap (8 one-warp blocks per SM). The two-row trip of shape 2
+// does not fit under the cap without spills; shape 3 stays available as an
+// option (and as the one-row form of the same pipeline).
 template <int K, int POL>
 __global__ void __maxnreg__(224) k_blocked_cap(const BlockedArgs a,
                                                                      const int64_t n0) {
