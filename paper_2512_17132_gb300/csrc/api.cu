@@ -197,12 +197,15 @@ int sm_count(fdtd_handle* h) {
 }
 
 // Cost of a general-path iteration of the blocked kernel in lean
-// iterations, as used by the segment planner. Measured on GB300: 7.5
-// balances the tasks best on config 2 (both polarisations) and is within
-// run-to-run noise of the best weight on the 6000-row config 5; the pipeline
-// is issue-bound and the general path (CPML recursion, source and monitor
-// terms, row checks) costs several lean ones.
-constexpr double kGeneralCost = 7.5;
+// iterations, per polarisation (S, P), as used by the segment planner. The
+// pipeline is issue-bound and the general path (CPML recursion, source and
+// monitor terms, row checks) costs many lean iterations; a P lean iteration
+// does more work (label-pair lookups of the edge coefficients), so its
+// ratio is lower. Measured on GB300 on config 2 (Gcell-updates/s, 8192
+// steps per run): S 7.5: 1301, 9: 1272, 10: 1351, 11: 1388, 12.5: 1101;
+// P 7.5: 967, 11: 899. Away from the best weight the cuts shift whole
+// general-path rows between tasks, so the response is uneven.
+constexpr double kGeneralCost[2] = {11.0, 7.5};
 
 // Estimated cost of one pipeline iteration t of the warp task of a segment
 // starting at y0: the kernel's lean-path test (blocked_task, is_fast) gives
@@ -217,14 +220,14 @@ double iteration_cost(const fdtd_grid& g, int K, int t, double wg) {
 }
 
 // Segment boundaries for about ny/seg segments of equal estimated cost for
-// K steps per launch. Every boundary lies in [K, ny) (a segment's K halo
-// rows above it exist) and none falls on r_row + 1 or t_row + 1 (the
-// segment owning a monitor row also owns the row below it, whose Hx enters
-// the row average).
-std::vector<int> segment_bounds(const fdtd_grid& g, int seg, int K) {
+// K steps per launch and polarisation pol. Every boundary lies in [K, ny)
+// (a segment's K halo rows above it exist) and none falls on r_row + 1 or
+// t_row + 1 (the segment owning a monitor row also owns the row below it,
+// whose Hx enters the row average).
+std::vector<int> segment_bounds(const fdtd_grid& g, int seg, int K, int pol) {
     const int ny = g.ny;
     const int n_target = std::max(1, (int)std::lround((double)ny / std::max(seg, 1)));
-    const double wg = kGeneralCost;
+    const double wg = kGeneralCost[pol ? 1 : 0];
     // prefix sums of the iteration costs: a segment [y0, y1) costs
     // C(y1 + K) - C(t_begin(y0))
     std::vector<double> C((size_t)ny + K + 1, 0.0);
@@ -332,7 +335,7 @@ BlockPlan& get_plan(fdtd_handle* h, int K) {
         }
     }
     seg = std::max(seg, min_seg);
-    const std::vector<int> b = segment_bounds(g, seg, K);
+    const std::vector<int> b = segment_bounds(g, seg, K, h->src.polarization);
     p.n_segs = (int)b.size() - 1;
     p.seg_rows = seg;
     CK(cudaMalloc(&p.d_seg_y0, b.size() * sizeof(int)));

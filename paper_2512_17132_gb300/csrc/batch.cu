@@ -142,7 +142,8 @@ void build_plan(fdtd_batch* b, int K, int variant, int seg_req) {
         // ceil(ny / seg) segments of at most seg rows (the wave model's count)
         const int n_s = std::max(1, (h->g.ny + seg - 1) / seg);
         const int seg_s = (h->g.ny + n_s - 1) / n_s;
-        const std::vector<int> bounds = segment_bounds(h->g, std::max(seg_s, K + 1), K);
+        const std::vector<int> bounds =
+            segment_bounds(h->g, std::max(seg_s, K + 1), K, h->src.polarization);
         int* d = nullptr;
         BCK(cudaMalloc(&d, bounds.size() * sizeof(int)));
         BCK(cudaMemcpy(d, bounds.data(), bounds.size() * sizeof(int), cudaMemcpyHostToDevice));

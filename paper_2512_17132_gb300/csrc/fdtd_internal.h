@@ -132,7 +132,7 @@ void compute_tables(fdtd_handle* h, int64_t upto);
 void upload_tables(fdtd_handle* h, int64_t upto);
 int sm_count(fdtd_handle* h);
 void sync_all(fdtd_handle* h);
-std::vector<int> segment_bounds(const fdtd_grid& g, int seg, int K);
+std::vector<int> segment_bounds(const fdtd_grid& g, int seg, int K, int pol);
 BlockPlan& get_plan(fdtd_handle* h, int K);
 
 }  // namespace fdtd
