@@ -605,9 +605,14 @@ def main():
                          "peak_kind": f"{peak_kind} copy bandwidth",
                          "algorithmic_bytes_per_launch": algo_bytes,
                          "avg_launch_ms": avg_launch_s * 1e3,
+                         "dram_gbs": (traffic / avg_launch_s / 1e9)
+                                     if traffic and avg_launch_s > 0 else None,
+                         "dram_frac": (traffic / avg_launch_s / 1e9 / peak)
+                                      if traffic and avg_launch_s > 0 and peak else None,
                          "note": "achieved = 25 B x cells x steps per launch / event-timed launch "
                                  "duration; temporal blocking moves fewer DRAM bytes than "
-                                 "that, so frac > 1 is possible (effective fraction)"},
+                                 "that, so frac > 1 is possible (effective fraction); "
+                                 "dram_gbs = ncu DRAM bytes per launch / the same duration"},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches),
             "rt_last": {"lambda_nm": results[-1][0] * 1e9, "R": results[-1][1][0],
                         "T": results[-1][1][1]},
