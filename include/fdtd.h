@@ -277,6 +277,31 @@ int fdtd_backward(fdtd_handle* h, double wR, double wT, double* g_eps, double* g
  * device) for later handles. Synchronises. */
 int fdtd_autotune(fdtd_handle* h, int32_t trial_launches);
 
+/* Row segments of the blocked kernel's load-balancing plan (host only; no
+ * device is touched, so it also runs where no GPU is present). The paper
+ * has no counterpart: this is the planner of this implementation's warp
+ * tasks, exposed for inspection and tests. For grid g (its rows checked as
+ * by fdtd_create), about ny / seg_rows segments (seg_rows below
+ * block_steps + 1 is raised to it), block_steps K in 1..8 and polarisation
+ * FDTD_POL_S or FDTD_POL_P it writes the row boundaries
+ * 0 = b[0] < b[1] < ... < b[n] = ny to out[0..n] and returns n + 1.
+ * The cuts minimise, to within a quarter of a lean iteration, the largest
+ * estimated segment cost over plans of at most N = round(ny / seg_rows)
+ * segments; segments are then split at their cost midpoints, costliest
+ * first, while fewer than N exist and one can be split. Iteration t of the
+ * warp task of segment [y0, y1) (t from y0 - K, or from 0 for the first
+ * segment, to y1 + K - 1) costs 1 when the rows t-K..t-1 it updates are
+ * all in 1..ny-P-1, outside the top CPML rows 0..P-1, and miss tfsf_row,
+ * r_row, r_row + 1, t_row and t_row + 1; otherwise it costs a fixed
+ * per-polarisation weight (the general path). Every inner boundary is >= K
+ * and differs from r_row + 1 and t_row + 1. Errors: FDTD_EINVAL for a bad
+ * grid, K or polarisation, or cap < n + 1; FDTD_ENOMEM when host memory
+ * runs out (message in fdtd_last_error(NULL)). The handle path cuts the
+ * same plan for the segment height its wave model picks
+ * (fdtd_stats.seg_rows). */
+int fdtd_plan_segments(const fdtd_grid* g, int32_t seg_rows, int32_t block_steps,
+                       int32_t polarization, int32_t* out, int32_t cap);
+
 /* Batched runs of independent simulations (the paper runs one simulation
  * per wavelength, polarisation and slice, Sec. 2.2 and Sec. 4; here they
  * share the GPU). A batch groups existing handles (same device, nx % 4 == 0

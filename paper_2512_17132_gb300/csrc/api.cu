@@ -1188,6 +1188,36 @@ int fdtd_get_stats(fdtd_handle* h, fdtd_stats* out) {
     return FDTD_OK;
 }
 
+int fdtd_plan_segments(const fdtd_grid* g, int32_t seg_rows, int32_t block_steps,
+                       int32_t polarization, int32_t* out, int32_t cap) {
+    auto fail = [](const char* msg) {
+        g_create_err = msg;
+        return FDTD_EINVAL;
+    };
+    if (!g || !out) return fail("fdtd_plan_segments: null argument");
+    if (g->nx < 1 || g->ny < 8) return fail("grid: need nx >= 1 and ny >= 8");
+    if (g->pml_cells < 0) return fail("grid: pml_cells < 0");
+    if (!(g->r_row >= g->pml_cells && g->r_row < g->tfsf_row && g->tfsf_row < g->t_row &&
+          g->t_row + 1 < g->ny - g->pml_cells && g->tfsf_row >= 1))
+        return fail("grid: need pml_cells <= r_row < tfsf_row < t_row < ny - pml_cells - 1");
+    if (block_steps < 1 || block_steps > fdtd::blocked_max_K())
+        return fail("fdtd_plan_segments: block_steps must be 1..8");
+    if (polarization != FDTD_POL_S && polarization != FDTD_POL_P)
+        return fail("fdtd_plan_segments: polarization must be FDTD_POL_S or FDTD_POL_P");
+    std::vector<int> b;
+    try {
+        b = fdtd::segment_bounds(*g, std::max(seg_rows, block_steps + 1), block_steps,
+                                 polarization);
+    } catch (const std::bad_alloc&) {
+        g_create_err = "fdtd_plan_segments: out of host memory";
+        return FDTD_ENOMEM;
+    }
+    if ((int64_t)b.size() > cap) return fail("fdtd_plan_segments: cap below the boundary count");
+    std::copy(b.begin(), b.end(), out);
+    g_create_err.clear();
+    return (int)b.size();
+}
+
 const char* fdtd_last_error(const fdtd_handle* h) {
     return h ? h->err.c_str() : g_create_err.c_str();
 }

@@ -88,6 +88,8 @@ def load_library(path: str = LIB_PATH):
         "fdtd_forward_checkpointed": (C.c_int, [vp, i64, i32]),
         "fdtd_backward": (C.c_int, [vp, C.c_double, C.c_double, vp, vp, vp, dp]),
         "fdtd_autotune": (C.c_int, [vp, i32]),
+        "fdtd_plan_segments": (C.c_int, [C.POINTER(fdtd_grid), i32, i32, i32,
+                                         C.POINTER(C.c_int32), i32]),
         "fdtd_batch_create": (C.c_int, [C.POINTER(vp), i32, C.POINTER(vp)]),
         "fdtd_batch_set_option": (C.c_int, [vp, i32, i64]),
         "fdtd_batch_autotune": (C.c_int, [vp, i32]),
@@ -230,6 +232,18 @@ def fdtd_bloch_propagating(h) -> int:
     r = int(load_library().fdtd_bloch_propagating(h))
     _check(min(r, 0), h)
     return r
+
+
+def fdtd_plan_segments(grid: fdtd_grid, seg_rows: int, block_steps: int,
+                       polarization: int = FDTD_POL_S) -> np.ndarray:
+    """Row boundaries of the blocked kernel's segment plan (host only)."""
+    lib = load_library()
+    cap = int(grid.ny) + 1
+    out = (C.c_int32 * cap)()
+    r = int(lib.fdtd_plan_segments(C.byref(grid), int(seg_rows), int(block_steps),
+                                   int(polarization), out, cap))
+    _check(min(r, 0), None)
+    return np.frombuffer(out, dtype=np.int32, count=r).copy()
 
 
 BLOCH_FIELDS = ("R_flux", "T_flux", "R_paper", "T_paper", "R_corr", "T_corr", "w", "ky")
