@@ -1,0 +1,122 @@
+"""Write the oracle's R, T, DFT lines and sampled fields for full-size runs.
+
+Calls only oracle/ and fdtd_inputs/: every stored value comes from the FP64
+oracle (its time loop in C, bit-identical to the numpy loop). The GPU tests
+and bench.py compare the CUDA library with these files.
+
+  python tests/golden/make_oracle_goldens.py c2 550 [450 662 800 1450] [--threads N]
+      config 2: the 2000 x 12500 dicot cross-section (seed 0), 30 000 steps
+      at each wavelength (nm), S polarisation, as the throughput line runs it.
+  python tests/golden/make_oracle_goldens.py c3crop [--threads N]
+      config 3 (healthy monocot, 550 nm, dx = 15 nm) cropped to its first
+      8192 rows (the whole leaf and both monitors) and 2048 columns, with R, T
+      and the DFT lines after 4000 and after 60 000 steps.
+
+Each run writes oracle_<case>.json (scalars, with the command that made
+them) and oracle_<case>.npz (the four DFT lines, complex128, in the order
+Ez(r_row), Hx(r_row), Ez(t_row), Hx(t_row), and the fields Ez, Hx, Hy at
+4096 cells drawn with numpy's default_rng(2024), with their flat indices).
+"""
+from __future__ import annotations
+
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from fdtd_inputs import config_c2, config_c3, crop_layout  # noqa: E402
+from oracle.fdtd_tmz import empty_twin  # noqa: E402
+from oracle.fdtd_tmz_c import TMzOracleC  # noqa: E402
+
+N_SAMPLES = 4096
+SAMPLE_SEED = 2024
+
+
+def sample_index(ny, nx):
+    return np.sort(np.random.default_rng(SAMPLE_SEED).choice(ny * nx, N_SAMPLES, replace=False))
+
+
+def c3_crop_spec(**kw):
+    """Config 3 healthy at 550 nm, first 8192 rows and 2048 columns."""
+    return crop_layout(config_c3(550e-9, **kw), 8192, 2048)
+
+
+def _record(name, spec, leaf, twin, steps, wall, threads, cmd, extra=None):
+    p_up, p_down = leaf.fluxes()
+    p_inc = twin.fluxes()[1] * spec.nx
+
+    def ratio(x):
+        # None until the incident pulse has reached t_row (P_inc = 0)
+        return x / p_inc if p_inc > 0.0 else None
+
+    rec = dict(
+        case=name, nx=spec.nx, ny=spec.ny, dx=spec.dx, dt=spec.dt, steps=int(steps),
+        lambda0=spec.lambda0, r_row=spec.r_row, t_row=spec.t_row, tfsf_row=spec.tfsf_row,
+        polarization="S (TMz)", R=ratio(p_up), T=ratio(p_down),
+        A=None if p_inc <= 0.0 else 1.0 - (p_up + p_down) / p_inc, p_up=p_up, p_down=p_down, p_inc=p_inc,
+        oracle="FP64 oracle (TMzOracle state, C time loop TMzOracleC)",
+        threads=int(threads), wall_s=round(wall, 1), command=cmd)
+    if extra:
+        rec.update(extra)
+    idx = sample_index(spec.ny, spec.nx)
+    d = leaf.dft
+    np.savez_compressed(
+        os.path.join(HERE, f"oracle_{name}.npz"),
+        dft=np.stack([d["e_r"], d["h_r"], d["e_t"], d["h_t"]]),
+        idx=idx, ez=leaf.ez.ravel()[idx], hx=leaf.hx.ravel()[idx], hy=leaf.hy.ravel()[idx],
+        max_abs=np.array([np.abs(leaf.ez).max(), np.abs(leaf.hx).max(), np.abs(leaf.hy).max()]))
+    with open(os.path.join(HERE, f"oracle_{name}.json"), "w") as f:
+        json.dump(rec, f, indent=1)
+    print(json.dumps({k: rec[k] for k in ("case", "steps", "R", "T", "A", "wall_s")}), flush=True)
+
+
+def run_c2(lam_nm, threads):
+    spec = config_c2(lam_nm * 1e-9)
+    t = time.time()
+    leaf = TMzOracleC(spec).run(spec.steps, threads)
+    twin = empty_twin(spec).run(spec.steps)
+    _record(f"c2_{lam_nm:g}nm", spec, leaf, twin, spec.steps, time.time() - t, threads,
+            f"python tests/golden/make_oracle_goldens.py c2 {lam_nm:g} --threads {threads}",
+            dict(seed=0))
+
+
+def run_c3crop(threads):
+    spec = c3_crop_spec()
+    t = time.time()
+    leaf = TMzOracleC(spec)
+    twin = empty_twin(spec)
+    done = 0
+    for steps in (4000, 60000):
+        leaf.run(steps - done, threads)
+        twin.run(steps - done)
+        done = steps
+        _record(f"c3crop_{steps}", spec, leaf, twin, steps, time.time() - t, threads,
+                f"python tests/golden/make_oracle_goldens.py c3crop --threads {threads}",
+                dict(seed=0, crop="config 3 healthy, rows 0-8191, columns 0-2047"))
+
+
+def main(argv):
+    threads = os.cpu_count() or 1
+    if "--threads" in argv:
+        k = argv.index("--threads")
+        threads = int(argv[k + 1])
+        argv = argv[:k] + argv[k + 2:]
+    case = argv[0]
+    if case == "c2":
+        for lam in argv[1:] or ["550"]:
+            run_c2(float(lam), threads)
+    elif case == "c3crop":
+        run_c3crop(threads)
+    else:
+        raise SystemExit(__doc__)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:])
