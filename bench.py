@@ -9,7 +9,10 @@ and the flux reduction to R and T. Steps cycle through the five wavelengths
 (independent runs, weak scaling, no collective on the data path).
 
 `--impl reference` times the FP64 oracle on the host cores instead, on a
-bounded sample of the same workload (a few leapfrog steps per bench step).
+bounded sample of the same workload (100 leapfrog steps per bench step of
+its C time loop on all cores). The default line also carries one config-5
+gradient pass (the adjoint's Gcell-updates/s), the oracle on the host cores
+and the R/T error of the timed runs against stored full-length oracle runs.
 """
 from __future__ import annotations
 
@@ -47,8 +50,14 @@ def parse_args():
     p.add_argument("--kernel", type=int, default=0)
     p.add_argument("--block-steps", type=int, default=0)
     p.add_argument("--seg-rows", type=int, default=0)
+    p.add_argument("--variant", type=int, default=-1,
+                   help="blocked-kernel code shape (default: the library's choice)")
+    p.add_argument("--plan-weight", type=float, default=0.0,
+                   help="segment planner weight of a general-path iteration (0: default)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-adjoint", action="store_true",
+                   help="skip the config-5 adjoint pass of the default line")
     p.add_argument("--pol", default="s", choices=["s", "p"],
                    help="polarisation of the runs: s (TMz, the default) or p (TEz)")
     return p.parse_args()
@@ -222,28 +231,38 @@ def run_reference(args):
     if rank != 0:
         return 0
     spec = workload(args, WAVELENGTHS[1])
-    sim = _oracle_class(spec)(spec)
-    sample_steps = 2 if args.config != "c1" else 200
+    cores = os.cpu_count() or 1
+    if getattr(spec, "polarization", 0):
+        # P polarisation: the numpy TEz oracle (one core)
+        sim, cores = _oracle_class(spec)(spec), 1
+        advance = lambda n: [sim.step() for _ in range(n)]
+        how = "numpy FP64 TEz oracle, single-threaded elementwise"
+    else:
+        from oracle.fdtd_tmz_c import TMzOracleC
+        sim = TMzOracleC(spec)
+        advance = lambda n: sim.run(n, cores)
+        how = "the oracle's C time loop, FP64, OpenMP over rows on all cores"
+    sample_steps = 100 if args.config != "c1" else 4000
+    if cores == 1 and args.config != "c1":
+        sample_steps = 2
     for _ in range(args.warmup):
-        for _ in range(sample_steps):
-            sim.step()
+        advance(sample_steps)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        for _ in range(sample_steps):
-            sim.step()
+        advance(sample_steps)
     dt = time.perf_counter() - t0
     cells = spec.nx * spec.ny
     value = cells * sample_steps * args.steps / dt / 1e9
     sample = (f"{sample_steps} leapfrog steps of the {spec.nx}x{spec.ny} grid per bench step "
-              f"(numpy FP64, single-threaded elementwise)")
+              f"({how})")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": describe(spec, args),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample, "cpu_model": cpu_model(), "nproc": os.cpu_count()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -273,19 +292,30 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def measured_traffic(spec, block_steps):
-    """DRAM bytes per launch of the blocked kernel from the committed ncu
-    summary, scaled to this grid; None when the kernel changed since."""
+def plan_hash(fdtd, spec, seg_rows, block_steps):
+    """Hash and segment count of the blocked kernel's segment plan for this
+    grid (the library's host-only plan query, default planner weight)."""
+    pol = int(getattr(spec, "polarization", 0))
+    b = fdtd.fdtd_plan_segments(fdtd.make_grid(spec), seg_rows, block_steps, pol)
+    return hashlib.sha256(b.tobytes()).hexdigest()[:16], int(len(b) - 1)
+
+
+def measured_counters(spec, block_steps, variant, plan_sha):
+    """DRAM bytes and warp instructions per launch of the blocked kernel from
+    the committed ncu record, or None when the kernel source, the depth, the
+    code shape or the segment plan differ from those the counters were
+    taken with."""
     path = os.path.join(ROOT, "profiles", "blocked_stencil_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
     except Exception:
         return None
-    if d.get("kernel_src_sha") != kernel_source_hash() or d.get("block_steps") != block_steps:
+    if (d.get("kernel_src_sha") != kernel_source_hash() or d.get("block_steps") != block_steps
+            or d.get("variant") != variant or d.get("plan_sha") != plan_sha
+            or d.get("cells") != spec.nx * spec.ny):
         return None
-    per_cell = d["dram_bytes_per_launch"] / d["cells"]
-    return per_cell * spec.nx * spec.ny
+    return d
 
 
 def peaks():
@@ -295,6 +325,136 @@ def peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def roofline_record(achieved, peak, peak_kind, algo_bytes, avg_launch_s, traffic, inst, clk):
+    """Roofline of the blocked stencil. frac is the effective HBM fraction
+    (algorithmic bytes of the launch's K steps over its event-timed
+    duration): temporal blocking moves about 1/K of those bytes, so it can
+    exceed 1. What binds is instruction issue: issue_frac = ncu warp
+    instructions per launch / (launch time x SMs x 4 schedulers x the
+    sampled SM clock); dram_frac is the real DRAM traffic (ncu bytes per
+    launch over the same duration) against the measured copy bandwidth."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = (clk or {}).get("sm_mhz") or None
+    ok = avg_launch_s and avg_launch_s > 0
+    issue_peak = sms * 4 * mhz * 1e6 if mhz else None
+    return {
+        "bound": "issue", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "frac": (achieved / peak) if achieved else None, "frac_kind": "effective",
+        "traffic": traffic, "peak_kind": f"{peak_kind} copy bandwidth",
+        "algorithmic_bytes_per_launch": algo_bytes, "avg_launch_ms": avg_launch_s * 1e3,
+        "dram_gbs": (traffic / avg_launch_s / 1e9) if traffic and ok else None,
+        "dram_frac": (traffic / avg_launch_s / 1e9 / peak) if traffic and ok and peak else None,
+        "warp_inst_per_launch": inst,
+        "issue_rate_ginst_s": (inst / avg_launch_s / 1e9) if inst and ok else None,
+        "issue_peak_ginst_s": issue_peak / 1e9 if issue_peak else None,
+        "issue_frac": (inst / avg_launch_s / issue_peak) if inst and ok and issue_peak else None,
+        "note": "frac = 25 B x cells x steps per launch / event-timed launch duration / measured "
+                "copy bandwidth (effective: temporal blocking moves fewer DRAM bytes); "
+                "dram_frac and issue_frac use the ncu counters of the same kernel, plan and "
+                "depth (null when the source, shape or plan changed since they were taken); "
+                "issue peak = SMs x 4 schedulers x 1 warp instruction per clock x sampled SM clock"}
+
+
+def golden_rt_check(results, steps):
+    """R and T of the timed runs against the FP64 oracle's values for the
+    same full-length config-2 runs (tests/golden), where they exist."""
+    errs = []
+    for lam, (R, T) in results:
+        path = os.path.join(ROOT, "tests", "golden", f"oracle_c2_{lam * 1e9:g}nm.json")
+        try:
+            with open(path) as f:
+                g = json.load(f)
+        except Exception:
+            continue
+        if g.get("steps") != steps or g.get("R") is None:
+            continue
+        errs.append((lam, abs(R - g["R"]), abs(T - g["T"])))
+    if not errs:
+        return None
+    return {"max_abs_err_R": max(e[1] for e in errs), "max_abs_err_T": max(e[2] for e in errs),
+            "runs_checked": len(errs),
+            "wavelengths_nm": sorted({round(e[0] * 1e9) for e in errs}),
+            "vs": "FP64 oracle, same full-length runs (tests/golden/oracle_c2_*.json)",
+            "bound": 2e-3}
+
+
+def adjoint_pass(fdtd, torch):
+    """One config-5 gradient pass (1000 x 6000 cells, 30 000 steps,
+    checkpoints every 500): the checkpointed forward and the discrete
+    adjoint of R(550 nm), each timed with the CUDA-synchronised wall clock
+    (the handle runs on the library's own streams). The adjoint's roofline
+    is 90 algorithmic bytes per reverse cell-update."""
+    import fdtd_inputs as fi
+    spec = fi.config_c5()
+    cells = spec.nx * spec.ny * spec.steps
+    with fdtd.Simulation(spec) as sim:
+        fdtd.fdtd_forward_checkpointed(sim.h, 2000, 500)          # warm-up
+        fdtd.fdtd_backward(sim.h, 1.0, 0.0, spec.ny, spec.nx, len(spec.materials))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fdtd.fdtd_forward_checkpointed(sim.h, spec.steps, 500)
+        R, T = sim.flux()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        fdtd.fdtd_backward(sim.h, 1.0, 0.0, spec.ny, spec.nx, len(spec.materials))
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+    peak, kind = peaks()
+    adj = cells / (t2 - t1) / 1e9
+    return {"value": adj, "unit": UNIT, "ms": (t2 - t1) * 1e3,
+            "roofline_frac": adj / (peak / 90.0),
+            "roofline": f"{peak / 90.0:.1f} Gcell-updates/s = {kind} copy bandwidth / 90 B",
+            "forward_checkpointed": {"value": cells / (t1 - t0) / 1e9, "unit": UNIT,
+                                     "ms": (t1 - t0) * 1e3},
+            "workload": f"config 5: {spec.nx}x{spec.ny} cells, {spec.steps} steps, dR(550 nm)/d"
+                        "(eps_r, sigma, n, k), checkpoints every 500 steps",
+            "timing": "CUDA-synchronised wall clock", "R": R}
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=5).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline(spec, budget_s=8.0):
+    """The oracle timed on this machine's host cores on a bounded sample of
+    the same grid: its C time loop on all cores (OpenMP over rows) and the
+    numpy loop on one core."""
+    from oracle.fdtd_tmz_c import TMzOracleC
+    cores = os.cpu_count() or 1
+    sim = TMzOracleC(spec)
+    sim.run(2, cores)
+    n, t0 = 0, time.perf_counter()
+    while n < 4 or time.perf_counter() - t0 < budget_s:
+        sim.run(8, cores)
+        n += 8
+    dt = time.perf_counter() - t0
+    rate = spec.nx * spec.ny * n / dt / 1e9
+    r1, n1, s1 = oracle_rate(spec, budget_s=budget_s)
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} leapfrog steps of the {spec.nx}x{spec.ny} grid in {dt:.1f} s "
+                      f"(the oracle's C time loop, FP64, OpenMP over rows on all cores)",
+            "cpu_model": cpu_model(), "nproc": cores,
+            "single_core": {"value": r1, "unit": UNIT, "cores": 1,
+                            "sample": f"{n1} leapfrog steps in {s1:.1f} s (numpy oracle, "
+                                      "single-threaded elementwise)"}}
 
 
 def run_c4(args):
@@ -531,6 +691,10 @@ def main():
         s = fdtd.Simulation(sp, stream=stream, kernel=args.kernel,
                             block_steps=args.block_steps or None,
                             seg_rows=args.seg_rows or None, timing=True)
+        if args.variant >= 0:
+            fdtd.fdtd_set_option(s.h, fdtd.FDTD_OPT_VARIANT, args.variant)
+        if args.plan_weight > 0:
+            fdtd.fdtd_set_option(s.h, fdtd.FDTD_OPT_PLAN_WEIGHT, round(args.plan_weight * 1000))
         sims[lam] = s
     results = []
 
@@ -573,8 +737,14 @@ def main():
     algo_bytes = BYTES_PER_CELL_UPDATE * spec0.nx * spec0.ny * steps_per_launch
     peak, peak_kind = peaks()
     achieved = algo_bytes / avg_launch_s / 1e9 if avg_launch_s > 0 else None
-    # the stored DRAM traffic was captured on the S kernel
-    traffic = measured_traffic(spec0, steps_per_launch) if kern == 2 and args.pol == "s" else None
+    # the stored counters were captured on the S kernel with the default plan
+    counters = None
+    if kern == 2 and args.pol == "s" and args.plan_weight <= 0:
+        p_sha, n_segs = plan_hash(fdtd, spec0, st["seg_rows"], steps_per_launch)
+        counters = measured_counters(spec0, steps_per_launch, st["variant"], p_sha)
+    traffic = counters["dram_bytes_per_launch"] if counters else None
+    inst = counters.get("warp_inst_per_launch") if counters else None
+    rt_check = golden_rt_check([(lam, rt) for lam, rt in results[W:]], spec0.steps)
     for s in sims.values():
         s.close()
 
@@ -607,18 +777,19 @@ def main():
                        "fdtd_flux + fdtd_destroy; h2d = label map, material table, "
                        "incident/phase tables"}
 
+    adjoint = None
+    if rank == 0 and world == 1 and not args.no_adjoint and args.pol == "s":
+        adjoint = adjoint_pass(fdtd, torch)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        sp = specs[order[-1]]
-        rate, n_s, secs = oracle_rate(sp)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{n_s} leapfrog steps of the {sp.nx}x{sp.ny} grid in {secs:.1f} s "
-                         f"(numpy FP64, single-threaded elementwise)"}
+        cpu = cpu_baseline(specs[order[-1]])
 
     if rank == 0:
         cfg = describe(spec0, args)
         cfg.update({"kernel": "temporally blocked" if kern == 2 else "per-half-step",
                     "steps_per_launch": steps_per_launch, "seg_rows": st["seg_rows"],
+                    "code_shape": st["variant"],
                     "parallelism": f"{world} independent run stream(s), one per GPU"})
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
@@ -626,23 +797,13 @@ def main():
             "wall_ms_per_step": wall / K * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": cfg,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": (achieved / peak) if achieved else None,
-                         "traffic": traffic,
-                         "peak_kind": f"{peak_kind} copy bandwidth",
-                         "algorithmic_bytes_per_launch": algo_bytes,
-                         "avg_launch_ms": avg_launch_s * 1e3,
-                         "dram_gbs": (traffic / avg_launch_s / 1e9)
-                                     if traffic and avg_launch_s > 0 else None,
-                         "dram_frac": (traffic / avg_launch_s / 1e9 / peak)
-                                      if traffic and avg_launch_s > 0 and peak else None,
-                         "note": "achieved = 25 B x cells x steps per launch / event-timed launch "
-                                 "duration; temporal blocking moves fewer DRAM bytes than "
-                                 "that, so frac > 1 is possible (effective fraction); "
-                                 "dram_gbs = ncu DRAM bytes per launch / the same duration"},
+            "roofline": roofline_record(achieved, peak, peak_kind, algo_bytes, avg_launch_s,
+                                        traffic, inst, clk),
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches),
             "rt_last": {"lambda_nm": results[-1][0] * 1e9, "R": results[-1][1][0],
                         "T": results[-1][1][1]},
+            "rt_check": rt_check,
+            "adjoint": adjoint,
         }
         print(json.dumps(line))
     if world > 1:

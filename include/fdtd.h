@@ -122,7 +122,8 @@ typedef struct fdtd_stats {
     int32_t kernel;           /* stencil in use: 1 naive, 2 temporally blocked */
     int32_t block_steps;      /* steps per blocked launch */
     int32_t seg_rows;         /* rows per warp task of the blocked kernel */
-    int32_t reserved;
+    int32_t variant;          /* blocked-kernel code shape in use (FDTD_OPT_VARIANT) */
+    int32_t graph;            /* batches: 1 when captured CUDA graphs replay the launches */
 } fdtd_stats;
 
 /* Options for fdtd_set_option. */
@@ -133,10 +134,16 @@ typedef struct fdtd_stats {
 #define FDTD_OPT_WATCHDOG 5    /* check fields for non-finite values every N steps (0 off) */
 #define FDTD_OPT_VARIANT 6     /* blocked-kernel code shape: 0 one row per loop trip with a register
                                   prefetch, 1 two rows per trip, 2 rows streamed through a
-                                  shared-memory ring by cp.async, two lean rows per trip
-                                  (default), 3 the ring with one row per trip, built under a
-                                  224-register cap; P handles run shapes 2 and 3 */
+                                  shared-memory ring by cp.async, two lean rows per trip, 3 the
+                                  ring with one row per trip, built under a 224-register cap,
+                                  5 shape 2 with a label-pair coefficient table and paired FP32
+                                  instructions (S polarisation, at most 16 labels). Default: 5
+                                  where allowed, else 2; P handles run shapes 2 and 3; 4 is
+                                  internal (EINVAL) */
 #define FDTD_OPT_GRAPH 7       /* batches: replay captured CUDA graphs of launch chunks (default 1) */
+#define FDTD_OPT_PLAN_WEIGHT 8 /* segment planner: cost of a general-path iteration of the blocked
+                                  kernel in lean iterations, times 1000 (0: the measured default,
+                                  11 for S and 7.5 for P); batches take each handle's value */
 
 /* Create a simulation. grid, labels (ny*nx uint8, values < n_labels), table
  * (n_labels entries, n > k >= 0) and source are copied; the caller keeps
@@ -316,7 +323,7 @@ int fdtd_plan_segments(const fdtd_grid* g, int32_t seg_rows, int32_t block_steps
  * later work on them waits for the batch. Options: FDTD_OPT_BLOCK_STEPS,
  * FDTD_OPT_SEG_ROWS, FDTD_OPT_VARIANT, FDTD_OPT_TIMING, FDTD_OPT_GRAPH.
  * fdtd_batch_autotune times candidate launch shapes on the whole batch like
- * fdtd_autotune (state unchanged). Stats: reserved = 1 when a graph is in use.
+ * fdtd_autotune (state unchanged). Stats: graph = 1 when a graph is in use.
  * Errors of fdtd_batch_create are reported by fdtd_batch_last_error(NULL). */
 typedef struct fdtd_batch fdtd_batch;
 int fdtd_batch_create(fdtd_handle* const* hs, int32_t n, fdtd_batch** out);
@@ -327,29 +334,38 @@ int fdtd_batch_get_stats(fdtd_batch* b, fdtd_stats* out);
 const char* fdtd_batch_last_error(const fdtd_batch* b);
 void fdtd_batch_destroy(fdtd_batch* b);
 
-/* Allocation-free stepping (the paper has no counterpart: it is an interface
- * for callers that cannot call cudaMalloc where they step the fields, e.g.
- * code running during CUDA stream capture, plug-ins confined to a device
- * memory budget handed out by their host framework, or processes whose
- * device allocator belongs to another runtime).
+/* Allocation-free stepping. The paper has no counterpart: this is an
+ * interface for callers that may not call cudaMalloc where they step the
+ * fields, such as a plug-in confined to a device-memory budget that its host
+ * framework hands out, or a process whose device memory belongs to another
+ * runtime's allocator (a framework's caching allocator that already holds
+ * the GPU). fdtd_create and fdtd_run allocate their state and tables; this
+ * call uses only buffers the caller owns plus a static scratch array.
  *
  * Advances a source-free field state by `steps` (1..8) leapfrog steps with
- * the temporally blocked kernel, on `cuda_stream` (NULL = legacy stream), and
- * allocates nothing: the kernel's scratch (segment table, coefficient and
- * CPML tables, zeroed source tables, a sink for monitor sums) lives in one
- * static 8 MiB device array per GPU, held by every GPU that loads the
- * library until the process exits. Grids needing more scratch (roughly
- * nx > 130000, or pml_cells > 64) are rejected with FDTD_EINVAL and a
- * message.
+ * the temporally blocked kernel (code shape 5 for at most 16 labels, else
+ * 2) on `cuda_stream` (NULL = legacy stream), and allocates nothing: the
+ * kernel's scratch (segment table, coefficient and CPML tables, zeroed
+ * source tables, a sink for monitor sums) lives in one static 8 MiB device
+ * array per GPU, held by every GPU that loads the library until the process
+ * exits. Grids needing more scratch (roughly nx > 130000, or pml_cells > 64)
+ * are rejected with FDTD_EINVAL and a message.
  *   grid: layout as for fdtd_create (nx % 4 == 0 required); table/n_labels/
  *     lambda0: materials at the wavelength (coefficients as in fdtd_create);
- *   labels: device, ny*nx uint8, values < n_labels (not checked here);
- *   in[5], out[5]: device buffers {Ez, eta0*Hx, eta0*Hy, psi_E, psi_H}:
- *     fields dense ny*nx FP32 (Ez in V/m, H scaled by eta0 = mu0 c0, i.e.
- *     also V/m), CPML carries dense (2*pml_cells)*nx FP32 (top rows first,
- *     zero at the start of a run); outputs must not alias inputs; the caller
- *     owns all of them. Hx row 0 stays as given (the fixed top edge).
+ *   labels: device, ny*nx uint8, values < n_labels (not checked here),
+ *     4-byte aligned;
+ *   in[5], out[5]: device buffers {Ez, eta0*Hx, eta0*Hy, psi_E, psi_H},
+ *     16-byte aligned: fields dense ny*nx FP32 (Ez in V/m, H scaled by
+ *     eta0 = mu0 c0, i.e. also V/m), CPML carries dense (2*pml_cells)*nx
+ *     FP32 (top rows first, zero at the start of a run); outputs must not
+ *     alias inputs; the caller owns all of them. Hx row 0 stays as given
+ *     (the fixed top edge).
  *   err/err_len: optional buffer for a message on failure.
+ * A call launches two kernels on the stream: the first copies the tables,
+ * computed on the host and passed by value as its launch parameters, into
+ * the scratch array and clears its zeroed parts; the second steps the
+ * fields. No host memory is read after the call returns, and the call does
+ * not wait for earlier work on the stream.
  * The first call on a device looks up the array's device address with that
  * device current; make that first call before any stream capture begins.
  * Every call shares the one array and overwrites it, so calls that overlap

@@ -207,6 +207,10 @@ int sm_count(fdtd_handle* h) {
 // general-path rows between tasks, so the response is uneven.
 constexpr double kGeneralCost[2] = {11.0, 7.5};
 
+double general_cost(int pol, double override_w) {
+    return override_w > 0.0 ? override_w : kGeneralCost[pol ? 1 : 0];
+}
+
 // Estimated cost of one pipeline iteration t of the warp task of a segment
 // starting at y0: the kernel's lean-path test (blocked_task, is_fast) gives
 // 1, the general path `wg` lean iterations. A segment [y0, y1) runs the
@@ -224,10 +228,10 @@ double iteration_cost(const fdtd_grid& g, int K, int t, double wg) {
 // (a segment's K halo rows above it exist) and none falls on r_row + 1 or
 // t_row + 1 (the segment owning a monitor row also owns the row below it,
 // whose Hx enters the row average).
-std::vector<int> segment_bounds(const fdtd_grid& g, int seg, int K, int pol) {
+std::vector<int> segment_bounds(const fdtd_grid& g, int seg, int K, int pol, double weight) {
     const int ny = g.ny;
     const int n_target = std::max(1, (int)std::lround((double)ny / std::max(seg, 1)));
-    const double wg = kGeneralCost[pol ? 1 : 0];
+    const double wg = general_cost(pol, weight);
     // prefix sums of the iteration costs: a segment [y0, y1) costs
     // C(y1 + K) - C(t_begin(y0))
     std::vector<double> C((size_t)ny + K + 1, 0.0);
@@ -304,13 +308,14 @@ BlockPlan& get_plan(fdtd_handle* h, int K) {
     if ((int)h->plans.size() <= K) h->plans.resize(K + 1);
     BlockPlan& p = h->plans[K];
     const int want_seg = h->opt_seg;
-    if (p.K == K && p.d_seg_y0 && p.variant == h->opt_variant &&
+    if (p.K == K && p.d_seg_y0 && p.variant == h->opt_variant && p.weight == h->opt_weight &&
         (want_seg == 0 || want_seg == p.seg_rows))
         return p;
     dfree(p.d_seg_y0);
     const fdtd_grid& g = h->g;
     p.K = K;
     p.variant = h->opt_variant;
+    p.weight = h->opt_weight;
     p.halo = (K + 3) / 4 * 4;
     p.w_int = 128 - 2 * p.halo;
     p.n_strips = (g.nx + p.w_int - 1) / p.w_int;
@@ -335,7 +340,7 @@ BlockPlan& get_plan(fdtd_handle* h, int K) {
         }
     }
     seg = std::max(seg, min_seg);
-    const std::vector<int> b = segment_bounds(g, seg, K, h->src.polarization);
+    const std::vector<int> b = segment_bounds(g, seg, K, h->src.polarization, h->opt_weight);
     p.n_segs = (int)b.size() - 1;
     p.seg_rows = seg;
     CK(cudaMalloc(&p.d_seg_y0, b.size() * sizeof(int)));
@@ -564,6 +569,9 @@ static int create_impl(const fdtd_grid* grid, const uint8_t* labels, const fdtd_
         REQUIRE(source->polarization == FDTD_POL_S || source->polarization == FDTD_POL_P,
                 "source: polarization must be FDTD_POL_S (0) or FDTD_POL_P (1)");
         const bool pol_p = source->polarization == FDTD_POL_P;
+        // default code shape of the blocked kernel: 5 (label-pair table,
+        // paired FP32) where the labels fit the pair table, else 2
+        h->opt_variant = pair_shape_ok(pol_p, maps, n_labels) ? 5 : 2;
         REQUIRE(!pol_p || (!maps && n_labels <= 16),
                 "source: P polarisation needs a label map with at most 16 labels");
         REQUIRE(source->lambda0 > 0, "source: lambda0 must be positive");
@@ -1156,8 +1164,15 @@ int fdtd_set_option(fdtd_handle* h, int32_t option, int64_t value) {
             if (value < 0) break;
             h->opt_watchdog = value;
             return FDTD_OK;
+        case FDTD_OPT_PLAN_WEIGHT:
+            if (value < 0 || value > 1000000) break;
+            h->opt_weight = value / 1000.0;
+            return FDTD_OK;
         case FDTD_OPT_VARIANT:
-            if (value < 0 || value > 3) break;
+            if (value < 0 || value > 6 || value == 4) break;
+            if (value >= 5 && !pair_shape_ok(h->src.polarization == FDTD_POL_P, h->maps,
+                                             h->n_labels))
+                break;
             h->opt_variant = (int)value;
             return FDTD_OK;
         default:
@@ -1184,7 +1199,8 @@ int fdtd_get_stats(fdtd_handle* h, fdtd_stats* out) {
     for (auto& p : h->plans)
         if (p.K == h->opt_block) seg = p.seg_rows;
     out->seg_rows = seg;
-    out->reserved = 0;
+    out->variant = h->opt_variant;
+    out->graph = 0;
     return FDTD_OK;
 }
 

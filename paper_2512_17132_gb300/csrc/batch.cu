@@ -97,6 +97,13 @@ void drop_plan(fdtd_batch* b) {
     b->planned = false;
 }
 
+// Code shape 5 needs every simulation of the batch to allow it.
+bool batch_pair_ok(const fdtd_batch* b) {
+    for (const auto* h : b->hs)
+        if (!pair_shape_ok(h->src.polarization == FDTD_POL_P, h->maps, h->n_labels)) return false;
+    return true;
+}
+
 // Wave model over the union of the batch: waves x (rows + 2K), each
 // simulation cut into ceil(ny / rows) segments so that no task is longer.
 int model_seg(fdtd_batch* b, int K, int variant) {
@@ -143,7 +150,7 @@ void build_plan(fdtd_batch* b, int K, int variant, int seg_req) {
         const int n_s = std::max(1, (h->g.ny + seg - 1) / seg);
         const int seg_s = (h->g.ny + n_s - 1) / n_s;
         const std::vector<int> bounds =
-            segment_bounds(h->g, std::max(seg_s, K + 1), K, h->src.polarization);
+            segment_bounds(h->g, std::max(seg_s, K + 1), K, h->src.polarization, h->opt_weight);
         int* d = nullptr;
         BCK(cudaMalloc(&d, bounds.size() * sizeof(int)));
         BCK(cudaMemcpy(d, bounds.data(), bounds.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -304,9 +311,10 @@ int batch_tune(fdtd_batch* b, int trials) {
     double best = -1;
     int bK = b->K, bv = b->variant, bs = 0;
     for (int K : {8, 7, 6}) {
-        for (int v : {0, 1, 2, 3}) {
+        for (int v : {0, 1, 2, 3, 5}) {
             if (K == 8 && v == 1) continue;          // exceeds the register file at K = 8
             if (b->hs[0]->src.polarization && v < 2) continue;   // P: shapes 2 and 3 only
+            if (v == 5 && !batch_pair_ok(b)) continue;
             const int s0 = model_seg(b, K, v);
             for (int f : {-1, 0, 1}) {
                 const int seg = f < 0 ? std::max(1, (s0 * 2) / 3) : (f > 0 ? (s0 * 3) / 2 : s0);
@@ -366,6 +374,8 @@ int fdtd_batch_create(fdtd_handle* const* hs, int32_t n, fdtd_batch** out) {
         configure_twin_batch();
         b->K = std::min(hs[0]->opt_block, blocked_max_K());
         b->variant = hs[0]->opt_variant;
+        if (b->variant == 6) b->variant = 5;      // batches have no capped pair shape
+        if (b->variant == 5 && !batch_pair_ok(b)) b->variant = 2;
         *out = b;
         return FDTD_OK;
     } catch (const Fail& f) {
@@ -392,7 +402,8 @@ int fdtd_batch_set_option(fdtd_batch* b, int32_t option, int64_t value) {
             b->seg = (int)value;
             return FDTD_OK;
         case FDTD_OPT_VARIANT:
-            if (value < 0 || value > 2) break;
+            if (value < 0 || value > 5 || value == 4) break;
+            if (value == 5 && !batch_pair_ok(b)) break;
             b->variant = (int)value;
             return FDTD_OK;
         case FDTD_OPT_TIMING:
@@ -545,7 +556,8 @@ int fdtd_batch_get_stats(fdtd_batch* b, fdtd_stats* out) {
     out->kernel = 2;
     out->block_steps = b->planned ? b->pK : b->K;
     out->seg_rows = b->planned ? b->seg_used : b->seg;
-    out->reserved = b->graph ? 1 : 0;
+    out->variant = b->variant;
+    out->graph = b->graph ? 1 : 0;
     return FDTD_OK;
 }
 

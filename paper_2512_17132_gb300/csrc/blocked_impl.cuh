@@ -86,10 +86,84 @@ struct Pipe {
 
 struct Lane {
     const float2* coef;
+    const float4* pair;   // code shape 5: label-pair table (shared memory)
     int gx, y0, y1, ny, P, nx;
     bool own, own_r, own_t;
     float S;
 };
+
+// Code shape 5 (S polarisation, at most 16 labels) keeps, in place of the
+// packed label word of a row, the byte offsets of the label-pair table
+// entries of the lane's column pairs (0, 1) and (2, 3), 16 bits each. Entry
+// b0 | b1 << 4 holds (ca[b0], ca[b1], cb[b0], cb[b1]), the coefficients of
+// two neighbouring cells with labels b0 and b1 as two register pairs.
+__device__ __forceinline__ uint32_t pair_offsets(uint32_t w) {
+    return ((w | (w >> 4)) & 0x00ff00ffu) << 4;
+}
+__device__ __forceinline__ float4 pair_at(const float4* tab, uint32_t off) {
+    return *reinterpret_cast<const float4*>(reinterpret_cast<const char*>(tab) + off);
+}
+
+// (ca, cb) of column q of a lane from its row's label word.
+// Code shapes that use the label-pair table (S polarisation).
+template <int V>
+constexpr bool kPairShape = (V == 5 || V == 6);
+
+template <int V>
+__device__ __forceinline__ float2 coef_s(const Lane& ln, uint32_t w, int q) {
+    if (kPairShape<V>) {
+        const float4 c = pair_at(ln.pair, q < 2 ? (w & 0xffffu) : (w >> 16));
+        return (q & 1) ? make_float2(c.y, c.w) : make_float2(c.x, c.z);
+    }
+    return ln.coef[(w >> (8 * q)) & 0xffu];
+}
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+// Lean S iteration of code shape 5 with paired FP32 instructions
+// (fma/add/mul .f32x2): a lane's columns (0, 1) and (2, 3) form the pairs.
+// Each element of a paired instruction rounds exactly as the scalar _rn
+// intrinsic, and a - b is formed as fma(b, -1, a), which rounds like a
+// subtraction, so the results are bit for bit those of advance(). The
+// differences along x take a column pair shifted by one and stay scalar.
+template <int K>
+__device__ __forceinline__ void advance_lean_pair(Pipe<K>& p, float (&fE)[4], float (&fX)[4],
+                                                  float (&fY)[4], uint32_t& fL, const Lane& ln) {
+    const float2 S2 = f2(ln.S, ln.S);
+    const float2 M1 = f2(-1.0f, -1.0f);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const uint32_t cL = p.L[k];
+        const float4 c01 = pair_at(ln.pair, cL & 0xffffu);
+        const float4 c23 = pair_at(ln.pair, cL >> 16);
+        const float yR = __shfl_down_sync(FULL, p.Y[k][0], 1);
+        const float2 dhx01 = __ffma2_rn(f2(p.X[k][0], p.X[k][1]), M1, f2(fX[0], fX[1]));
+        const float2 dhx23 = __ffma2_rn(f2(p.X[k][2], p.X[k][3]), M1, f2(fX[2], fX[3]));
+        const float2 dhy01 = f2(__fsub_rn(p.Y[k][1], p.Y[k][0]), __fsub_rn(p.Y[k][2], p.Y[k][1]));
+        const float2 dhy23 = f2(__fsub_rn(p.Y[k][3], p.Y[k][2]), __fsub_rn(yR, p.Y[k][3]));
+        const float2 e01 = __ffma2_rn(f2(c01.z, c01.w), __fadd2_rn(dhy01, dhx01),
+                                      __fmul2_rn(f2(c01.x, c01.y), f2(p.E[k][0], p.E[k][1])));
+        const float2 e23 = __ffma2_rn(f2(c23.z, c23.w), __fadd2_rn(dhy23, dhx23),
+                                      __fmul2_rn(f2(c23.x, c23.y), f2(p.E[k][2], p.E[k][3])));
+        const float2 d01 = __ffma2_rn(f2(p.E[k + 1][0], p.E[k + 1][1]), M1, e01);
+        const float2 d23 = __ffma2_rn(f2(p.E[k + 1][2], p.E[k + 1][3]), M1, e23);
+        const float2 x01 = __ffma2_rn(S2, d01, f2(p.X[k][0], p.X[k][1]));
+        const float2 x23 = __ffma2_rn(S2, d23, f2(p.X[k][2], p.X[k][3]));
+        const float eL = __shfl_up_sync(FULL, e23.y, 1);
+        const float2 dy01 = f2(__fsub_rn(e01.x, eL), __fsub_rn(e01.y, e01.x));
+        const float2 dy23 = f2(__fsub_rn(e23.x, e01.y), __fsub_rn(e23.y, e23.x));
+        const float2 y01 = __ffma2_rn(S2, dy01, f2(p.Y[k][0], p.Y[k][1]));
+        const float2 y23 = __ffma2_rn(S2, dy23, f2(p.Y[k][2], p.Y[k][3]));
+        // level k now waits at row r+1; the new level-(k+1) row r flows up
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { p.E[k][q] = fE[q]; p.X[k][q] = fX[q]; p.Y[k][q] = fY[q]; }
+        fE[0] = e01.x; fE[1] = e01.y; fE[2] = e23.x; fE[3] = e23.y;
+        fX[0] = x01.x; fX[1] = x01.y; fX[2] = x23.x; fX[3] = x23.y;
+        fY[0] = y01.x; fY[1] = y01.y; fY[2] = y23.x; fY[3] = y23.y;
+        p.L[k] = fL;
+        fL = cL;
+    }
+}
 
 // One iteration of the pipeline: level k advances at row t-k-1, k = 0..K-1.
 // GENERAL = false is the lean path for iterations whose K rows hold no
@@ -100,6 +174,10 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
                                         float (&fY)[4], uint32_t& fL, const int t,
                                         const BlockedArgs& a, const Lane& ln, float4* ringE,
                                         float4* ringH, const int64_t n0) {
+    if constexpr (!GENERAL && kPairShape<V> && POL == 0) {
+        advance_lean_pair<K>(p, fE, fX, fY, fL, ln);
+        return;
+    }
     const float S = ln.S;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -137,7 +215,7 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
                 }
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const float2 cc = POL ? make_float2(1.0f, S) : ln.coef[(cL >> (8 * q)) & 0xffu];
+                    const float2 cc = POL ? make_float2(1.0f, S) : coef_s<V>(ln, cL, q);
                     const float dhy = __fsub_rn(q < 3 ? p.Y[k][q + 1] : yR, p.Y[k][q]);
                     float dhx = __fsub_rn(fX[q], p.X[k][q]);
                     if (tf) dhx = __fsub_rn(dhx, hinc);
@@ -155,7 +233,7 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
             } else {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const float2 cc = POL ? make_float2(1.0f, S) : ln.coef[(cL >> (8 * q)) & 0xffu];
+                    const float2 cc = POL ? make_float2(1.0f, S) : coef_s<V>(ln, cL, q);
                     const float dhy = __fsub_rn(q < 3 ? p.Y[k][q + 1] : yR, p.Y[k][q]);
                     float dhx = __fsub_rn(fX[q], p.X[k][q]);
                     if (tf) dhx = __fsub_rn(dhx, hinc);
@@ -276,16 +354,20 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
 // per loop trip on lean stretches; 3 the ring with one row per trip (built
 // under a register cap, see k_blocked_cap); 4 the ring, one row per trip,
 // that also stores the state after every intermediate step of the launch
-// (its owned rows) into BlockedArgs::tape, for the adjoint's recompute.
+// (its owned rows) into BlockedArgs::tape, for the adjoint's recompute;
+// 5 (S polarisation, at most 16 labels) shape 2 with the label-pair table
+// and paired FP32 instructions on the lean path (advance_lean_pair); 6 shape
+// 5 with one row per trip (built under a register cap, k_blocked_cap168).
 template <int K, int V, int POL>
-__device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float2* s_coef,
+__device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float4* s_tab,
                                              const int task, const int64_t n0) {
     constexpr int H = ((K + 3) / 4) * 4;
     const int lane = threadIdx.x & 31;
     const int strip = task % a.n_strips;
     const int seg = task / a.n_strips;
     Lane ln;
-    ln.coef = s_coef;
+    ln.coef = reinterpret_cast<const float2*>(s_tab);
+    ln.pair = s_tab;
     ln.y0 = a.seg_y0[seg];
     ln.y1 = a.seg_y0[seg + 1];
     ln.nx = a.s.nx; ln.ny = a.s.ny; ln.P = a.s.P; ln.S = a.s.S;
@@ -368,6 +450,7 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float2*
             float fE[4], fX[4], fY[4];
             const float4 e4 = ring[slot][0][lane], x4 = ring[slot][1][lane], y4 = ring[slot][2][lane];
             uint32_t fL = ring_l[slot][lane];
+            if (kPairShape<V>) fL = pair_offsets(fL);
             fE[0] = e4.x; fE[1] = e4.y; fE[2] = e4.z; fE[3] = e4.w;
             fX[0] = x4.x; fX[1] = x4.y; fX[2] = x4.z; fX[3] = x4.w;
             fY[0] = y4.x; fY[1] = y4.y; fY[2] = y4.z; fY[3] = y4.w;
@@ -383,7 +466,7 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float2*
         // rows the two register sets alternate and the copies disappear.
 #pragma unroll 1
         for (int t = t_begin; t < t_end;) {
-            if (V == 2 && t + 1 < t_end && is_fast(t) && is_fast(t + 1)) {
+            if ((V == 2 || V == 5) && t + 1 < t_end && is_fast(t) && is_fast(t + 1)) {
                 row(t, true);
                 row(t + 1, true);
                 t += 2;
@@ -441,14 +524,32 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float2*
     }
 }
 
+// Coefficients of a block in shared memory: the per-label (S) or per-label-
+// pair (P) float2 table, or for code shape 5 the S label-pair table of
+// float4 entries (ca[b0], ca[b1], cb[b0], cb[b1]) at index b0 | b1 << 4,
+// built from the per-label table (labels < 16).
+template <int V, int POL>
+__device__ __forceinline__ void load_coef_table(const StepArgs& s, float4* s_tab) {
+    if (kPairShape<V>) {
+        const int last = s.n_labels - 1;
+        for (int t = threadIdx.x; t < 256; t += 32) {
+            const float2 c0 = s.coef[min(t & 15, last)], c1 = s.coef[min(t >> 4, last)];
+            s_tab[t] = make_float4(c0.x, c1.x, c0.y, c1.y);
+        }
+    } else {
+        float2* s_coef = reinterpret_cast<float2*>(s_tab);
+        const int n_coef = POL ? 256 : s.n_labels;
+        for (int t = threadIdx.x; t < n_coef; t += 32) s_coef[t] = s.coef[t];
+    }
+    __syncwarp();
+}
+
 template <int K, int V, int POL>
 __device__ __forceinline__ void blocked_kernel_body(const BlockedArgs& a, const int64_t n0) {
-    __shared__ float2 s_coef[256];
-    const int n_coef = POL ? 256 : a.s.n_labels;
-    for (int t = threadIdx.x; t < n_coef; t += blockDim.x) s_coef[t] = a.s.coef[t];
-    __syncwarp();
+    __shared__ float4 s_tab[kPairShape<V> ? 256 : 128];
+    load_coef_table<V, POL>(a.s, s_tab);
     if ((int)blockIdx.x >= a.n_tasks) return;       // one warp per block and task
-    blocked_task<K, V, POL>(a, s_coef, blockIdx.x, n0);
+    blocked_task<K, V, POL>(a, s_tab, blockIdx.x, n0);
 }
 
 template <int K, int V, int POL>
@@ -466,10 +567,18 @@ __global__ void __maxnreg__(224) k_blocked_cap(const BlockedArgs a,
     blocked_kernel_body<K, 3, POL>(a, n0);
 }
 
+// Code shape 6: shape 5 with one row per loop trip, compiled under a
+// 168-register cap, so that 12 one-warp blocks (3 per scheduler) fit an SM;
+// meant for K <= 7 (at K = 8 the cap spills).
+template <int K>
+__global__ void __maxnreg__(168) k_blocked_cap168(const BlockedArgs a, const int64_t n0) {
+    blocked_kernel_body<K, 6, 0>(a, n0);
+}
+
 template <int K, int V, int POL>
 __device__ __forceinline__ void blocked_batch_body(const BatchArgs& b, const int step_off,
                                                    const int parity) {
-    __shared__ float2 s_coef[256];
+    __shared__ float4 s_tab[kPairShape<V> ? 256 : 128];
     __shared__ __align__(16) unsigned char s_raw[sizeof(BlockedArgs)];
     const int task = blockIdx.x;
     if (task >= b.n_tasks) return;
@@ -480,11 +589,9 @@ __device__ __forceinline__ void blocked_batch_body(const BatchArgs& b, const int
     for (int q = threadIdx.x; q < (int)(sizeof(BlockedArgs) / sizeof(int)); q += 32) d[q] = w[q];
     __syncwarp();
     const BlockedArgs& a = *reinterpret_cast<const BlockedArgs*>(s_raw);
-    const int n_coef = POL ? 256 : a.s.n_labels;
-    for (int t = threadIdx.x; t < n_coef; t += 32) s_coef[t] = a.s.coef[t];
-    __syncwarp();
+    load_coef_table<V, POL>(a.s, s_tab);
     const int64_t n0 = a.n_base + *b.step_base + step_off;
-    blocked_task<K, V, POL>(a, s_coef, task - b.first_task[sim], n0);
+    blocked_task<K, V, POL>(a, s_tab, task - b.first_task[sim], n0);
 }
 
 // Many independent simulations in one launch: the grid covers the union of

@@ -1,5 +1,5 @@
 // S-polarised (TMz) instances of the batched blocked kernel: code shapes
-// 0-3 at K = 1..8.
+// 0-3 and 5 at K = 1..8.
 #include "blocked_impl.cuh"
 
 namespace fdtd {
@@ -12,6 +12,7 @@ bool launch_blocked_batch_s(const BatchArgs& b, int K, int variant, int step_off
     case k:                                                                                    \
         if (variant == 3) k_blocked_batch_cap<k, 0><<<grid, 32, 0, st>>>(b, step_off, parity); \
         else if (variant == 2) k_blocked_batch<k, 2, 0><<<grid, 32, 0, st>>>(b, step_off, parity); \
+        else if (variant == 5) k_blocked_batch<k, 5, 0><<<grid, 32, 0, st>>>(b, step_off, parity); \
         else if (variant) k_blocked_batch<k, 1, 0><<<grid, 32, 0, st>>>(b, step_off, parity);  \
         else k_blocked_batch<k, 0, 0><<<grid, 32, 0, st>>>(b, step_off, parity);               \
         break;

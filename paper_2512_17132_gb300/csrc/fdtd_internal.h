@@ -57,6 +57,7 @@ struct BlockPlan {
     int n_segs = 0;
     int seg_rows = 0;
     int variant = -1;
+    double weight = 0.0;      // planner weight the plan was cut with (0: default)
     int* d_seg_y0 = nullptr;  // n_segs + 1 row boundaries
 };
 
@@ -118,6 +119,11 @@ void configure_twin_batch();
 void launch_twin_batch(const TwinArgs* tws, int n, int max_ny, int max_P,
                        const int64_t* step_base, int steps, cudaStream_t st);
 int blocked_max_K();
+// Code shape 5 (label-pair table, paired FP32): S polarisation, a label map
+// with at most 16 labels.
+inline bool pair_shape_ok(bool pol_p, bool maps, int n_labels) {
+    return !pol_p && !maps && n_labels <= 16;
+}
 int blocked_warps_per_sm(int K, int variant, int pol = 0);
 
 // host helpers shared by the handle, batch and tuning code (api.cu); they
@@ -132,7 +138,9 @@ void compute_tables(fdtd_handle* h, int64_t upto);
 void upload_tables(fdtd_handle* h, int64_t upto);
 int sm_count(fdtd_handle* h);
 void sync_all(fdtd_handle* h);
-std::vector<int> segment_bounds(const fdtd_grid& g, int seg, int K, int pol);
+// weight: cost of a general-path iteration in lean iterations (0: the
+// measured default of the polarisation)
+std::vector<int> segment_bounds(const fdtd_grid& g, int seg, int K, int pol, double weight = 0.0);
 BlockPlan& get_plan(fdtd_handle* h, int K);
 
 }  // namespace fdtd
@@ -191,6 +199,7 @@ struct fdtd_handle {
     std::vector<fdtd::BlockPlan> plans;
     // options
     int opt_kernel = 0, opt_block = 8, opt_seg = 0, opt_timing = 0, opt_variant = 2;
+    double opt_weight = 0.0;    // planner weight of a general-path iteration (0: default)
     int64_t opt_watchdog = 0;
     // stats
     int64_t n = 0;

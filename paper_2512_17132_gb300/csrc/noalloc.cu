@@ -1,19 +1,23 @@
 // fdtd_blocked_advance_noalloc: the temporally blocked stencil for callers
 // that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc at the point where they want to step
-// the fields: code that runs while a CUDA stream is being captured into a
-// graph, a plug-in that must live inside a fixed device-memory budget owned
-// by its host framework, or a process whose device allocator belongs to
-// another runtime. fdtd_create/fdtd_run allocate (state, tables, plans), so
-// this entry point takes every input and output buffer from the caller and
-// keeps its own scratch (the segment table, the coefficient and CPML tables,
-// zeroed source tables and a sink for monitor sums) in one
+// Some callers may not call cudaMalloc where they step the fields: a plug-in
+// that must stay inside a fixed device-memory budget owned by its host
+// framework, or a process whose device memory is managed by another
+// runtime's allocator (a framework's caching allocator that already holds
+// the GPU's memory). fdtd_create/fdtd_run allocate (state, tables, plans),
+// so this entry point takes every input and output buffer from the caller
+// and keeps its own scratch (the segment table, the coefficient and CPML
+// tables, zeroed source tables and a sink for monitor sums) in one
 // file-scope __device__ array of kScratchBytes. Every GPU that loads the
-// library holds that array until the process exits.
+// library holds that array until the process exits. A call launches two
+// kernels on the caller's stream: one that stages the host-computed tables
+// (passed by value as its parameters) into the array, and the blocked
+// stencil (code shape 5 for at most 16 labels, else 2).
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <mutex>
 
@@ -32,6 +36,31 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 // with that device current (in host code the symbol is only a stand-in).
 std::mutex g_mu;
 void* g_addr[kMaxDevices] = {};
+
+// Host-computed tables of one call, passed by value as kernel parameters
+// (about 22 KB, inside the 32 764-byte parameter limit).
+struct Staged {
+    float2 coef[256];
+    float pe[6 * kMaxPml], ph[6 * kMaxPml];
+    int bounds[kMaxSegs + 1];
+    int n_coef, n_bounds;
+};
+static_assert(sizeof(Staged) < 32000, "staging parameters exceed the kernel parameter limit");
+
+__global__ void k_stage(const Staged t, float2* coef, float* pe, float* ph, int* seg,
+                        unsigned char* zero_tab, size_t zero_tab_bytes, double2* dft,
+                        size_t n_dft) {
+    const size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t st = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = i0; i < (size_t)t.n_coef; i += st) coef[i] = t.coef[i];
+    for (size_t i = i0; i < (size_t)(6 * kMaxPml); i += st) {
+        pe[i] = t.pe[i];
+        ph[i] = t.ph[i];
+    }
+    for (size_t i = i0; i < (size_t)t.n_bounds; i += st) seg[i] = t.bounds[i];
+    for (size_t i = i0; i < zero_tab_bytes; i += st) zero_tab[i] = 0;
+    for (size_t i = i0; i < n_dft; i += st) dft[i] = make_double2(0.0, 0.0);
+}
 
 constexpr double kC0 = 299792458.0;
 constexpr double kPi = 3.14159265358979323846;
@@ -69,8 +98,13 @@ extern "C" int fdtd_blocked_advance_noalloc(const fdtd_grid* grid, const uint8_t
         return fail(err, err_len, FDTD_EINVAL, "CPML parameters out of range");
     if (n_labels < 1 || n_labels > 256 || !(lambda0 > 0))
         return fail(err, err_len, FDTD_EINVAL, "need 1..256 labels and lambda0 > 0");
+    if (reinterpret_cast<uintptr_t>(labels) % 4 != 0)
+        return fail(err, err_len, FDTD_EINVAL, "labels must be 4-byte aligned");
     for (int f = 0; f < 5; ++f) {
         if (!in[f] || !out[f]) return fail(err, err_len, FDTD_EINVAL, "null field buffer");
+        if (reinterpret_cast<uintptr_t>(in[f]) % 16 != 0 ||
+            reinterpret_cast<uintptr_t>(out[f]) % 16 != 0)
+            return fail(err, err_len, FDTD_EINVAL, "field buffers must be 16-byte aligned");
         for (int q = 0; q < 5; ++q)
             if ((const void*)in[f] == (const void*)out[q])
                 return fail(err, err_len, FDTD_EINVAL, "output buffers must not alias inputs");
@@ -115,12 +149,14 @@ extern "C" int fdtd_blocked_advance_noalloc(const fdtd_grid* grid, const uint8_t
     unsigned char* sb = static_cast<unsigned char*>(base);
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
 
-    // host-side tables on the stack (FP64 arithmetic rounded to FP32)
+    // host-side tables on the stack (FP64 arithmetic rounded to FP32), in
+    // the parameter block of the staging launch
     const double mu0 = 4.0e-7 * kPi;
     const double eps0 = 1.0 / (mu0 * kC0 * kC0);
     const double S = kC0 * g.dt / g.dx;
     const double omega = 2.0 * kPi * kC0 / lambda0;
-    float2 coef[256];
+    Staged tab{};
+    float2* coef = tab.coef;
     for (int l = 0; l < n_labels; ++l) {
         const double n = table[l].n, k = table[l].k;
         if (!(n > 0 && k >= 0 && n > k))
@@ -130,7 +166,8 @@ extern "C" int fdtd_blocked_advance_noalloc(const fdtd_grid* grid, const uint8_t
         const double beta = sig * g.dt / (2.0 * eps0 * eps);
         coef[l] = make_float2((float)((1.0 - beta) / (1.0 + beta)), (float)(S / (eps * (1.0 + beta))));
     }
-    float pe[6 * kMaxPml] = {}, ph[6 * kMaxPml] = {};
+    float* pe = tab.pe;
+    float* ph = tab.ph;
     auto prof = [&](double depth, float* b, float* c, float* ik) {
         const double x = depth / (double)P;
         const double xm = std::pow(x, g.pml_order);
@@ -154,7 +191,10 @@ extern "C" int fdtd_blocked_advance_noalloc(const fdtd_grid* grid, const uint8_t
     // segment plan: the same wave-count model as the handle path
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 148;
-    int per_sm = blocked_warps_per_sm(K, 0);
+    // code shape 5 (label-pair table, paired FP32) where the labels fit it,
+    // else 2, as for handles
+    const int shape = pair_shape_ok(false, false, n_labels) ? 5 : 2;
+    int per_sm = blocked_warps_per_sm(K, shape);
     if (per_sm <= 0) per_sm = 8;
     const int64_t W = (int64_t)sms * per_sm;
     const int min_seg = P + K + 1;
@@ -167,7 +207,7 @@ extern "C" int fdtd_blocked_advance_noalloc(const fdtd_grid* grid, const uint8_t
         if (cost < best - 1e-9) { best = cost; seg = (int)rows; }
     }
     seg = std::max(seg, min_seg);
-    int bounds[kMaxSegs + 1];
+    int* bounds = tab.bounds;
     int nb = 0;
     bounds[nb++] = 0;
     for (int pos = seg; pos < g.ny && nb < kMaxSegs; pos += seg) {
@@ -177,15 +217,20 @@ extern "C" int fdtd_blocked_advance_noalloc(const fdtd_grid* grid, const uint8_t
     }
     bounds[nb++] = g.ny;
 
-    cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(sb + off_coef, coef, n_labels * sizeof(float2), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(sb + off_pml_e, pe, sizeof pe, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(sb + off_pml_h, ph, sizeof ph, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(sb + off_seg, bounds, nb * sizeof(int), cudaMemcpyHostToDevice, st);
-    // no incident wave: the source tables must read zero; the monitor sink is
-    // cleared so that it cannot accumulate to non-finite values over calls
-    if (e == cudaSuccess) e = cudaMemsetAsync(sb + off_tab, 0, tab_bytes, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(sb + off_dft, 0, (size_t)4 * g.nx * sizeof(double2), st);
+    // The tables travel by value as the parameters of one staging launch,
+    // which copies them into the scratch array and clears the zeroed parts:
+    // nothing is read from host memory after this call returns.
+    tab.n_coef = n_labels;
+    tab.n_bounds = nb;
+    float2* d_coef = reinterpret_cast<float2*>(sb + off_coef);
+    float* d_pe = reinterpret_cast<float*>(sb + off_pml_e);
+    float* d_ph = reinterpret_cast<float*>(sb + off_pml_h);
+    int* d_seg = reinterpret_cast<int*>(sb + off_seg);
+    unsigned char* d_tab = sb + off_tab;
+    double2* d_dft = reinterpret_cast<double2*>(sb + off_dft);
+    k_stage<<<32, 256, 0, st>>>(tab, d_coef, d_pe, d_ph, d_seg, d_tab, tab_bytes, d_dft,
+                                (size_t)4 * g.nx);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         std::snprintf(msg, sizeof msg, "staging the tables: %s", cudaGetErrorString(e));
         return fail(err, err_len, FDTD_ECUDA, msg);
@@ -212,7 +257,8 @@ extern "C" int fdtd_blocked_advance_noalloc(const fdtd_grid* grid, const uint8_t
     a.n_strips = n_strips;
     a.n_tasks = n_strips * (nb - 1);
     a.w_int = w_int;
-    launch_blocked(a, K, 0, 0, st);
+    if (!launch_blocked(a, K, shape, 0, st))
+        return fail(err, err_len, FDTD_EINVAL, "no blocked kernel instance for this step count");
     e = cudaGetLastError();
     if (e != cudaSuccess) {
         std::snprintf(msg, sizeof msg, "launch: %s", cudaGetErrorString(e));

@@ -16,6 +16,7 @@ FDTD_OK, FDTD_EINVAL, FDTD_ENOMEM, FDTD_ECUDA = 0, -1, -2, -3
 FDTD_EUNSTABLE, FDTD_ETIMEOUT, FDTD_ESTATE = -4, -5, -6
 FDTD_OPT_KERNEL, FDTD_OPT_BLOCK_STEPS, FDTD_OPT_SEG_ROWS = 1, 2, 3
 FDTD_OPT_TIMING, FDTD_OPT_WATCHDOG, FDTD_OPT_VARIANT, FDTD_OPT_GRAPH = 4, 5, 6, 7
+FDTD_OPT_PLAN_WEIGHT = 8
 FDTD_POL_S, FDTD_POL_P = 0, 1
 KERNEL_AUTO, KERNEL_NAIVE, KERNEL_BLOCKED = 0, 1, 2
 
@@ -40,7 +41,7 @@ class fdtd_stats(C.Structure):
     _fields_ = [("steps", C.c_int64), ("stencil_launches", C.c_int64),
                 ("total_launches", C.c_int64), ("stencil_ms", C.c_double),
                 ("kernel", C.c_int32), ("block_steps", C.c_int32), ("seg_rows", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("variant", C.c_int32), ("graph", C.c_int32)]
 
 
 class FDTDError(RuntimeError):
@@ -300,7 +301,7 @@ def fdtd_set_option(h, option: int, value: int):
 def fdtd_get_stats(h) -> dict:
     st = fdtd_stats()
     _check(load_library().fdtd_get_stats(h, C.byref(st)), h)
-    return {k: getattr(st, k) for k, _ in fdtd_stats._fields_ if k != "reserved"}
+    return {k: getattr(st, k) for k, _ in fdtd_stats._fields_ if k != "graph"}
 
 
 def fdtd_last_error(h=None) -> str:
@@ -346,8 +347,8 @@ def fdtd_batch_run(b, steps: int):
 def fdtd_batch_get_stats(b) -> dict:
     st = fdtd_stats()
     _check_batch(load_library().fdtd_batch_get_stats(b, C.byref(st)), b)
-    d = {k: getattr(st, k) for k, _ in fdtd_stats._fields_ if k != "reserved"}
-    d["graph"] = bool(st.reserved)
+    d = {k: getattr(st, k) for k, _ in fdtd_stats._fields_}
+    d["graph"] = bool(st.graph)
     return d
 
 
@@ -401,11 +402,43 @@ class Batch:
             pass
 
 
+def _check_noalloc_tensors(grid: fdtd_grid, labels, inputs, outputs):
+    """Checks the caller's tensors before any launch: dtype, contiguity and
+    size first, then that each lives on the current CUDA device, so a host
+    tensor or a short buffer never reaches the kernel."""
+    def bad(msg):
+        raise FDTDError(FDTD_EINVAL, "fdtd_blocked_advance_noalloc: " + msg)
+
+    import torch
+    nx, ny, P = int(grid.nx), int(grid.ny), int(grid.pml_cells)
+    if len(inputs) != 5 or len(outputs) != 5:
+        bad("inputs and outputs are five tensors each")
+    want = [ny * nx] * 3 + [2 * P * nx] * 2
+    names = ("Ez", "eta0*Hx", "eta0*Hy", "psi_E", "psi_H")
+    if not isinstance(labels, torch.Tensor) or labels.dtype != torch.uint8:
+        bad("labels must be a uint8 tensor")
+    if not labels.is_contiguous() or labels.numel() < ny * nx:
+        bad(f"labels must be contiguous with at least {ny * nx} elements")
+    for side, ts in (("input", inputs), ("output", outputs)):
+        for t, n, nm in zip(ts, want, names):
+            if not isinstance(t, torch.Tensor) or t.dtype != torch.float32:
+                bad(f"{side} {nm} must be a float32 tensor")
+            if not t.is_contiguous() or t.numel() < max(n, 1):
+                bad(f"{side} {nm} must be contiguous with at least {n} elements")
+    for t in (labels, *inputs, *outputs):
+        if not t.is_cuda:
+            bad("every tensor must be on a CUDA device")
+        if t.device.index != torch.cuda.current_device():
+            bad("every tensor must be on the current CUDA device")
+
+
 def fdtd_blocked_advance_noalloc(grid: fdtd_grid, labels, materials, lambda0: float,
                                  inputs, outputs, steps: int, stream=None):
     """Allocation-free stepping (see include/fdtd.h): inputs/outputs are five
     device tensors each {Ez, eta0*Hx, eta0*Hy, psi_E, psi_H}; labels a device
-    uint8 tensor. Raises FDTDError with the library's message on failure."""
+    uint8 tensor. The tensors are checked first; raises FDTDError with the
+    library's message on failure."""
+    _check_noalloc_tensors(grid, labels, inputs, outputs)
     lib = load_library()
     mats = np.ascontiguousarray(materials, dtype=np.float64).reshape(-1, 2)
     table = (fdtd_material * len(mats))(*[fdtd_material(float(n), float(k)) for n, k in mats])

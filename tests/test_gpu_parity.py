@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 from fdtd_inputs import config_c1, config_c1b
-from gpu_common import OracleTrace, field_errors, lib, need_gpu, rel_l2
+from gpu_common import OracleTrace, component_errors, field_errors, lib, need_gpu, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -67,7 +67,10 @@ def _run_and_compare(fd, spec, tr, rt, kernel, K, seg=None):
     assert st["kernel"] == kernel
     e1 = field_errors(f1500, tr.snaps[1500], tr.max_norm)
     e2 = field_errors(f4000, tr.snaps[4000], tr.max_norm)
+    c1 = component_errors(f1500, tr.snaps[1500], tr.max_norm)
+    c2 = component_errors(f4000, tr.snaps[4000], tr.max_norm)
     print(f"{spec.name} kernel={kernel} K={K}: err1500={e1} err4000={e2} "
+          f"(Ez, Hx, Hy alone: {c1} / {c2}) "
           f"R={R:.7f}/{rt[0]:.7f} T={T:.7f}/{rt[1]:.7f}")
     assert max(e1) < FIELD_TOL and max(e2) < FIELD_TOL
     assert abs(R - rt[0]) < RT_TOL and abs(T - rt[1]) < RT_TOL
@@ -91,7 +94,9 @@ def test_config1b_fields_and_rt(fd, ref_c1b, kernel, K):
                                            (1, 17, 1), (6, 200, 0), (6, 33, 1), (3, 29, 1),
                                            (8, None, 2), (8, 27, 2), (7, 41, 2), (5, 19, 2),
                                            (3, 22, 2), (1, 18, 2), (8, None, 3), (7, None, 3),
-                                           (7, 41, 3), (6, 33, 3), (4, 31, 3), (1, 18, 3)])
+                                           (7, 41, 3), (6, 33, 3), (4, 31, 3), (1, 18, 3),
+                                           (8, None, 5), (8, 27, 5), (7, 41, 5), (6, 33, 5),
+                                           (5, 19, 5), (3, 22, 5), (2, 19, 5), (1, 18, 5)])
 def test_blocked_is_bitwise_equal_to_naive(fd, K, seg, variant):
     spec = config_c1b(steps=411)
     with fd.Simulation(spec, kernel=1) as a:
@@ -105,6 +110,25 @@ def test_blocked_is_bitwise_equal_to_naive(fd, K, seg, variant):
     for x, y in zip(fa, fb):
         assert np.array_equal(x, y)
     assert np.array_equal(da, db)
+
+
+def test_pair_shape_is_the_default_only_where_the_labels_fit(fd):
+    # code shape 5 needs S polarisation and at most 16 labels
+    spec = config_c1b(steps=8)
+    with fd.Simulation(spec, kernel=2) as a:
+        a.run(8)
+        assert a.stats()["variant"] == 5
+        with pytest.raises(fd.FDTDError):
+            fd.fdtd_set_option(a.h, fd.FDTD_OPT_VARIANT, 4)
+    mats = np.vstack([spec.materials, np.tile([[1.3, 0.0]], (14, 1))])   # 18 labels
+    lab = spec.labels.copy()
+    lab[100, 7] = 17
+    wide = spec.with_(materials=mats, labels=lab)
+    with fd.Simulation(wide, kernel=2) as b:
+        with pytest.raises(fd.FDTDError):
+            fd.fdtd_set_option(b.h, fd.FDTD_OPT_VARIANT, 5)
+        b.run(8)
+        assert b.stats()["variant"] == 2
 
 
 @pytest.mark.parametrize("nx,kernel", [(100, 2), (104, 2), (8, 2), (4, 2), (37, 1), (3, 1),
