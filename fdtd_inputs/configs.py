@@ -274,18 +274,27 @@ def crop_layout(spec: RunSpec, ny: int, nx: Optional[int] = None) -> RunSpec:
 
 
 def config_e2(l_over_lambda: float, steps: int = 40000, nx: int = 100, ny: int = 897,
-              pml_cells: int = 40, rel_bandwidth: float = 0.1) -> RunSpec:
+              pml_cells: int = 40, rel_bandwidth: float = 0.1, h: float = 0.01,
+              diameter: float = 0.3, n_cyl: float = 2.0) -> RunSpec:
     """Validation workload of Sec. 3: a periodic array of dielectric cylinders
-    (period L = 1 m = 100 cells at h = 0.01 m, diameter D = 0.3 m, n = 2) under
-    a normally incident S-polarised (TMz) wave, dt = 23.57 ps (Sec. 3 table).
-    The paper's unit cell is periodic in y with PML in x; here the same cell
-    is periodic in x with the CPML at top and bottom (axes rotated)."""
+    (period L = 1 m = 100 cells at h = 0.01 m, diameter D = 0.3 m, n = 2)
+    under a normally incident S-polarised (TMz) wave, dt = 23.57 ps (Sec. 3
+    table). The paper's unit cell is periodic in y with PML in x; here the
+    same cell is periodic in x with the CPML at top and bottom (axes
+    rotated). A finer cell h < 0.01 m scales the cell counts, the CPML
+    thickness and dt by 0.01 / h (the same Courant number, the same physical
+    domain); pass steps scaled alike for the same physical run time.
+    diameter (m) and n_cyl vary the cylinder for sensitivity studies."""
     from .geometry import cylinder_array_labels
-    dx = 0.01
+    f = 0.01 / h
+    if f != 1.0:
+        nx, ny, pml_cells = int(round(nx * f)), int(round(ny * f)), int(round(pml_cells * f))
+    dx = h
     lam = 1.0 / l_over_lambda
-    rows = dict(r_row=pml_cells + 10, tfsf_row=pml_cells + 20, t_row=ny - pml_cells - 12)
-    labels = cylinder_array_labels(nx, ny, radius_cells=15.0)
-    mats = np.array([[1.0, 0.0], [2.0, 0.0]])
+    rows = dict(r_row=pml_cells + int(round(10 * f)), tfsf_row=pml_cells + int(round(20 * f)),
+                t_row=ny - pml_cells - int(round(12 * f)))
+    labels = cylinder_array_labels(nx, ny, radius_cells=0.5 * diameter / h)
+    mats = np.array([[1.0, 0.0], [n_cyl, 0.0]])
     spec = _base("e2", nx, ny, dx, steps, lam, rows, labels, mats, pml_cells=pml_cells,
                  rel_bandwidth=rel_bandwidth)
-    return spec.with_(dt=23.57e-12)
+    return spec.with_(dt=23.57e-12 * h / 0.01)

@@ -62,7 +62,9 @@ extern "C" {
 #define FDTD_ENOMEM (-2)    /* device or host allocation failed */
 #define FDTD_ECUDA (-3)     /* a CUDA call failed */
 #define FDTD_EUNSTABLE (-4) /* the watchdog saw a non-finite field */
-#define FDTD_ETIMEOUT (-5)  /* a bounded device-side wait gave up */
+#define FDTD_EBOUNDS (-5)   /* debug builds (FDTD_DEBUG_BOUNDS): an in-kernel index check
+                               failed (the access was skipped) or a guard band around a
+                               device buffer was overwritten; the message names the sites */
 #define FDTD_ESTATE (-6)    /* state buffer of the wrong size or layout */
 
 /* Grid and row layout. Rows: 0 <= pml_cells; pml_cells <= r_row < tfsf_row;
@@ -143,7 +145,14 @@ typedef struct fdtd_stats {
 #define FDTD_OPT_GRAPH 7       /* batches: replay captured CUDA graphs of launch chunks (default 1) */
 #define FDTD_OPT_PLAN_WEIGHT 8 /* segment planner: cost of a general-path iteration of the blocked
                                   kernel in lean iterations, times 1000 (0: the measured default,
-                                  11 for S and 7.5 for P); batches take each handle's value */
+                                  12 for S and 7.5 for P); batches take each handle's value */
+#define FDTD_OPT_DEBUG_TABLE_LIMIT 9 /* debug builds only (else FDTD_EINVAL): the index checks
+                                  admit only this many incident/phase table entries (0: all
+                                  allocated), so a longer run trips the table check without
+                                  any out-of-range access; tests the checks end to end */
+#define FDTD_OPT_DEBUG_POKE_GUARD 10 /* debug builds only (else FDTD_EINVAL): value 1 writes one
+                                  byte into the guard band behind the Ez buffer, which the
+                                  next synchronising call must report as FDTD_EBOUNDS */
 
 /* Create a simulation. grid, labels (ny*nx uint8, values < n_labels), table
  * (n_labels entries, n > k >= 0) and source are copied; the caller keeps

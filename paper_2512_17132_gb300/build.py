@@ -4,6 +4,11 @@ Each .cu translation unit is compiled by its own nvcc process (in parallel)
 and the objects are linked into paper_2512_17132_gb300/libfdtd.so with the
 CUDA runtime linked statically, so the library loads on machines without a
 GPU driver (only a call that touches the device needs one).
+
+build(debug=True) makes libfdtd_debug.so instead: the same sources with
+FDTD_DEBUG_BOUNDS defined, i.e. in-kernel index checks that record a failure
+and skip the access, and guard bands around the device buffers, both
+reported by the next synchronising call as FDTD_EBOUNDS.
 """
 from __future__ import annotations
 
@@ -17,6 +22,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfdtd.so")
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(HERE, "libfdtd_debug.so")
 SOURCES = ["api.cu", "kernels.cu", "blocked.cu", "blocked_s.cu", "blocked_sb.cu", "blocked_p.cu",
            "batch.cu", "adjoint.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -42,14 +49,18 @@ def _stale(obj: str, src: str) -> bool:
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
-def build(verbose: bool = False, ptxas_info: bool = False, force: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, ptxas_info: bool = False, force: bool = False,
+          debug: bool = False) -> str:
+    bdir, lib = (BUILD_DEBUG, LIB_DEBUG) if debug else (BUILD, LIB)
+    os.makedirs(bdir, exist_ok=True)
     cc = nvcc()
     extra = ["-Xptxas", "-v"] if ptxas_info else []
+    if debug:
+        extra.append("-DFDTD_DEBUG_BOUNDS")
     jobs = []
     for s in SOURCES:
         src = os.path.join(CSRC, s)
-        obj = os.path.join(BUILD, s.replace(".cu", ".o"))
+        obj = os.path.join(bdir, s.replace(".cu", ".o"))
         if force or ptxas_info or _stale(obj, src):
             jobs.append([cc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj])
 
@@ -63,16 +74,17 @@ def build(verbose: bool = False, ptxas_info: bool = False, force: bool = False) 
                 sys.stderr.write(r.stdout + r.stderr)
             if r.returncode != 0:
                 raise RuntimeError(f"nvcc failed for {cmd[-3]}:\n{r.stdout}\n{r.stderr}")
-    objs = [os.path.join(BUILD, s.replace(".cu", ".o")) for s in SOURCES]
-    if jobs or not os.path.exists(LIB):
-        tmp = LIB + ".tmp"
+    objs = [os.path.join(bdir, s.replace(".cu", ".o")) for s in SOURCES]
+    if jobs or not os.path.exists(lib):
+        tmp = lib + ".tmp"
         cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose=True, ptxas_info="-v" in sys.argv, force="-f" in sys.argv))
+    print(build(verbose=True, ptxas_info="-v" in sys.argv, force="-f" in sys.argv,
+                debug="--debug" in sys.argv))

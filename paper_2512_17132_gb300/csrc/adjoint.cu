@@ -71,6 +71,8 @@ struct AdjArgs {
     float* gA; float* gB;   // FP32 per-segment sums
     const float* tE; const float* tX; const float* tY; const float* tPE;   // tape state of step n
     int n_coef;             // entries of coef (labelled handles)
+    int64_t n_tab;          // table entries valid on the device (debug index checks)
+    unsigned* dbg;          // error word of the debug index checks
 };
 
 __device__ __forceinline__ float2 cell_coef(const AdjArgs& a, int j, int i) {
@@ -81,7 +83,7 @@ __device__ __forceinline__ float2 cell_coef(const AdjArgs& a, int j, int i) {
 // monitor source of Hx^{n+1} at row j (rows jr, jr+1, jt, jt+1)
 __device__ __forceinline__ float src_h(const AdjArgs& a, int j, int i, int64_t n) {
     double s = 0.0;
-    const double2 ph = a.phH[n];
+    const double2 ph = tab_n(a.phH, n, a.n_tab, a.dbg);
     if (j == a.jr || j == a.jr + 1) {
         const double2 e = a.dft[i];
         s += 0.5 * a.kR * (e.x * ph.x + e.y * ph.y);
@@ -95,7 +97,7 @@ __device__ __forceinline__ float src_h(const AdjArgs& a, int j, int i, int64_t n
 
 __device__ __forceinline__ float src_e(const AdjArgs& a, int j, int i, int64_t n) {
     double s = 0.0;
-    const double2 pe = a.phE[n];
+    const double2 pe = tab_n(a.phE, n, a.n_tab, a.dbg);
     if (j == a.jr) {
         const double2 hh = a.dft[a.nx + i];
         s += a.kR * (hh.x * pe.x + hh.y * pe.y);
@@ -180,7 +182,7 @@ __global__ void k_adj_e(AdjArgs a, int64_t n, const float* __restrict__ lE_in,
     const float dhy = __fsub_rn(a.tY[(size_t)j * a.pitch + ir], a.tY[o]);
     const float hxb = (j + 1 < a.ny) ? a.tX[o + a.pitch] : 0.0f;
     float dhx = __fsub_rn(hxb, a.tX[o]);
-    if (j == a.js) dhx = __fsub_rn(dhx, a.hinc[n]);
+    if (j == a.js) dhx = __fsub_rn(dhx, tab_n(a.hinc, n, a.n_tab, a.dbg));
     const int pe = pml_e_index(j, a.ny, a.P);
     float curl;
     if (pe >= 0) {
@@ -361,7 +363,7 @@ __global__ void __launch_bounds__(256) k_adj_e4(AdjArgs a, int64_t n, const floa
     for (int q = 0; q < 4; ++q) {
         const float dhy = __fsub_rn(ty[q + 1], ty[q]);
         float dhx = __fsub_rn(x1[q], x0[q]);
-        if (j == a.js) dhx = __fsub_rn(dhx, a.hinc[n]);
+        if (j == a.js) dhx = __fsub_rn(dhx, tab_n(a.hinc, n, a.n_tab, a.dbg));
         if (pe >= 0) {
             const float b = a.pml_e[pe], cc = a.pml_e[2 * a.P + pe], ik = a.pml_e[4 * a.P + pe];
             const float psi = psi_new(b, cc, psi_old[q], dhx);
@@ -685,6 +687,8 @@ int fdtd_backward(fdtd_handle* h, double wR, double wT, double* g_eps, double* g
         const bool vec4 = (nx % 4 == 0);
         const dim3 grd4((nx / 4 + 255) / 256, ny);
         a.n_coef = h->n_labels;
+        a.n_tab = table_limit(h);
+        a.dbg = h->d_dbg;
         const int64_t n_seg = (steps + every - 1) / every;
         for (int64_t c = n_seg - 1; c >= 0; --c) {
             const int64_t c0 = c * every;

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <map>
+#include <mutex>
 #include <tuple>
 #include <cstdio>
 #include <cstring>
@@ -44,15 +45,51 @@ thread_local std::string g_create_err;
         }                                \
     } while (0)
 
+#ifdef FDTD_DEBUG_BOUNDS
+// Guarded allocations of debug builds: user pointer -> (allocation base,
+// user bytes), process-wide, so dfree finds the base of any buffer.
+std::mutex g_guard_mu;
+std::map<void*, std::pair<void*, size_t>> g_guarded;
+#endif
+
 template <typename T>
 void dalloc(fdtd_handle* h, T** p, size_t count) {
-    CK(cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(count, 1) * sizeof(T)));
-    CK(cudaMemsetAsync(*p, 0, std::max<size_t>(count, 1) * sizeof(T), h->stream));
+    const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+#ifdef FDTD_DEBUG_BOUNDS
+    const size_t user = (bytes + kGuardBytes - 1) / kGuardBytes * kGuardBytes;
+    unsigned char* base = nullptr;
+    CK(cudaMalloc(reinterpret_cast<void**>(&base), user + 2 * kGuardBytes));
+    CK(cudaMemsetAsync(base, kGuardByte, kGuardBytes, h->stream));
+    CK(cudaMemsetAsync(base + kGuardBytes + bytes, kGuardByte, user - bytes + kGuardBytes,
+                       h->stream));
+    *p = reinterpret_cast<T*>(base + kGuardBytes);
+    {
+        std::lock_guard<std::mutex> lk(g_guard_mu);
+        g_guarded[*p] = std::make_pair((void*)base, bytes);
+    }
+    h->guarded.push_back(*p);
+#else
+    CK(cudaMalloc(reinterpret_cast<void**>(p), bytes));
+#endif
+    CK(cudaMemsetAsync(*p, 0, bytes, h->stream));
 }
 
 template <typename T>
 void dfree(T*& p) {
-    if (p) cudaFree(p);
+    if (!p) return;
+#ifdef FDTD_DEBUG_BOUNDS
+    {
+        std::lock_guard<std::mutex> lk(g_guard_mu);
+        auto it = g_guarded.find((void*)p);
+        if (it != g_guarded.end()) {
+            cudaFree(it->second.first);
+            g_guarded.erase(it);
+            p = nullptr;
+            return;
+        }
+    }
+#endif
+    cudaFree(p);
     p = nullptr;
 }
 
@@ -82,7 +119,50 @@ StepArgs step_args(fdtd_handle* h) {
     a.pml_e = h->pml_e; a.pml_h = h->pml_h;
     a.hinc = h->d_hinc; a.einc = h->d_einc; a.phE = h->d_phE; a.phH = h->d_phH;
     a.dft = h->dft;
+    a.n_tab = table_limit(h);
+    a.n_coef = h->src.polarization == FDTD_POL_P ? 256 : h->n_labels;
+    a.dbg = h->d_dbg;
     return a;
+}
+
+int64_t table_limit(const fdtd_handle* h) {
+    return h->dbg_tab_limit > 0 ? std::min(h->tab_cap, h->dbg_tab_limit) : h->tab_cap;
+}
+
+void debug_checks(fdtd_handle* h) {
+#ifdef FDTD_DEBUG_BOUNDS
+    // guard bands of every buffer of the handle: bit 31 of the error word
+    for (void* u : h->guarded) {
+        std::pair<void*, size_t> g;
+        {
+            std::lock_guard<std::mutex> lk(g_guard_mu);
+            auto it = g_guarded.find(u);
+            if (it == g_guarded.end()) continue;
+            g = it->second;
+        }
+        const size_t user = (g.second + kGuardBytes - 1) / kGuardBytes * kGuardBytes;
+        const unsigned char* base = static_cast<const unsigned char*>(g.first);
+        launch_guard_check(base, kGuardBytes, kGuardByte, h->d_dbg, 31, h->stream);
+        launch_guard_check(base + kGuardBytes + g.second, user - g.second + kGuardBytes,
+                           kGuardByte, h->d_dbg, 31, h->stream);
+    }
+    unsigned word = 0;
+    CK(cudaMemcpyAsync(&word, h->d_dbg, sizeof word, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (word) {
+        static const char* names[8] = {"lane columns", "stored row", "CPML carry row",
+                                       "table entry", "monitor column", "label",
+                                       "adjoint tape row", "task"};
+        std::string msg = "debug checks failed:";
+        for (int b = 0; b < 8; ++b)
+            if (word & (1u << b)) msg += std::string(" [index check: ") + names[b] + "]";
+        if (word & (1u << 31)) msg += " [guard band overwritten]";
+        h->err = msg;
+        throw Fail{FDTD_EBOUNDS};
+    }
+#else
+    (void)h;
+#endif
 }
 
 // Grow the incident/phase tables so that steps [0, n_end) can be produced.
@@ -198,14 +278,14 @@ int sm_count(fdtd_handle* h) {
 
 // Cost of a general-path iteration of the blocked kernel in lean
 // iterations, per polarisation (S, P), as used by the segment planner. The
-// pipeline is issue-bound and the general path (CPML recursion, source and
-// monitor terms, row checks) costs many lean iterations; a P lean iteration
-// does more work (label-pair lookups of the edge coefficients), so its
-// ratio is lower. Measured on GB300 on config 2 (Gcell-updates/s, 8192
-// steps per run): S 7.5: 1301, 9: 1272, 10: 1351, 11: 1388, 12.5: 1101;
-// P 7.5: 967, 11: 899. Away from the best weight the cuts shift whole
-// general-path rows between tasks, so the response is uneven.
-constexpr double kGeneralCost[2] = {11.0, 7.5};
+// general path (CPML recursion, source and monitor terms, row checks) costs
+// many lean iterations; a P lean iteration does more work (label-pair
+// lookups of the edge coefficients), so its ratio is lower. Measured on
+// GB300 on config 2 (Gcell-updates/s, 8192 steps per run): S with code
+// shape 5 (the S default): 9: 1350, 10: 1462, 11: 1521, 12: 1543, 13: 1385,
+// 15: 1268; P 7.5: 967, 11: 899. Away from the best weight the cuts shift
+// whole general-path rows between tasks, so the response is uneven.
+constexpr double kGeneralCost[2] = {12.0, 7.5};
 
 double general_cost(int pol, double override_w) {
     return override_w > 0.0 ? override_w : kGeneralCost[pol ? 1 : 0];
@@ -423,6 +503,7 @@ void sync_all(fdtd_handle* h) {
     CK(cudaStreamSynchronize(h->twin_stream));
     CK(cudaStreamSynchronize(h->stream));
     collect_timing(h);
+    debug_checks(h);
     if (h->opt_watchdog > 0) {
         int flag = 0;
         CK(cudaMemcpy(&flag, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost));
@@ -452,7 +533,8 @@ void free_all(fdtd_handle* h) {
     for (auto& c : h->ck) dfree(c);
     h->ck.clear();
     dfree(h->tw_ez); dfree(h->tw_hx); dfree(h->tw_psiE); dfree(h->tw_psiH); dfree(h->tw_dft);
-    dfree(h->d_flux); dfree(h->d_flag);
+    dfree(h->d_flux); dfree(h->d_flag); dfree(h->d_dbg);
+    h->guarded.clear();
     dfree(h->d_hinc); dfree(h->d_einc); dfree(h->d_phE); dfree(h->d_phH);
     if (h->h_flux) cudaFreeHost(h->h_flux);
     if (h->h_hinc) cudaFreeHost(h->h_hinc);
@@ -643,6 +725,7 @@ static int create_impl(const fdtd_grid* grid, const uint8_t* labels, const fdtd_
         dalloc(h, &h->tw_dft, 4);
         dalloc(h, &h->d_flux, 4);
         dalloc(h, &h->d_flag, 4);
+        dalloc(h, &h->d_dbg, 1);
         CK(cudaMallocHost(&h->h_flux, 4 * sizeof(double)));
 
         // CPML tables [3][2P] for Ez rows and Hx rows
@@ -760,6 +843,7 @@ int fdtd_run(fdtd_handle* h, int64_t steps) {
         tw.hinc = h->d_hinc; tw.einc = h->d_einc; tw.phE = h->d_phE; tw.phH = h->d_phH;
         tw.ez = h->tw_ez; tw.hx = h->tw_hx; tw.psiE = h->tw_psiE; tw.psiH = h->tw_psiH;
         tw.dft = h->tw_dft;
+        tw.dbg = h->d_dbg;
         // chunks of whole blocked launches, so only the run's last launch is short
         const int64_t kb = (kern == 2) ? std::max(1, std::min(h->opt_block, blocked_max_K())) : 1;
         const int64_t chunk = std::max<int64_t>(kb, kChunk - kChunk % kb);
@@ -767,6 +851,7 @@ int fdtd_run(fdtd_handle* h, int64_t steps) {
         while (s < n_end) {
             const int64_t ce = std::min(n_end, s + chunk);
             produce_tables(h, std::max(ce, h->tab_uploaded));
+            tw.n_tab = table_limit(h);
             CK(cudaEventRecord(h->ev_tab, h->stream));
             CK(cudaStreamWaitEvent(h->twin_stream, h->ev_tab, 0));
             launch_twin(tw, s, (int)(ce - s), h->twin_stream);
@@ -1164,13 +1249,43 @@ int fdtd_set_option(fdtd_handle* h, int32_t option, int64_t value) {
             if (value < 0) break;
             h->opt_watchdog = value;
             return FDTD_OK;
+        case FDTD_OPT_DEBUG_TABLE_LIMIT:
+#ifdef FDTD_DEBUG_BOUNDS
+            if (value < 0) break;
+            h->dbg_tab_limit = value;
+            return FDTD_OK;
+#else
+            h->err = "fdtd_set_option: FDTD_OPT_DEBUG_TABLE_LIMIT needs a debug build";
+            return FDTD_EINVAL;
+#endif
+        case FDTD_OPT_DEBUG_POKE_GUARD:
+#ifdef FDTD_DEBUG_BOUNDS
+            // one byte of the guard band behind the current Ez buffer (a host
+            // write into the allocation), which the next check must report
+            if (value != 1) break;
+            {
+                std::pair<void*, size_t> g{nullptr, 0};
+                {
+                    std::lock_guard<std::mutex> lk(g_guard_mu);
+                    auto it = g_guarded.find((void*)h->ez[h->cur]);
+                    if (it != g_guarded.end()) g = it->second;
+                }
+                if (!g.first) break;
+                unsigned char* at = static_cast<unsigned char*>(g.first) + kGuardBytes + g.second;
+                if (cudaMemsetAsync(at, 0, 1, h->stream) != cudaSuccess) return FDTD_ECUDA;
+            }
+            return FDTD_OK;
+#else
+            h->err = "fdtd_set_option: FDTD_OPT_DEBUG_POKE_GUARD needs a debug build";
+            return FDTD_EINVAL;
+#endif
         case FDTD_OPT_PLAN_WEIGHT:
             if (value < 0 || value > 1000000) break;
             h->opt_weight = value / 1000.0;
             return FDTD_OK;
         case FDTD_OPT_VARIANT:
-            if (value < 0 || value > 6 || value == 4) break;
-            if (value >= 5 && !pair_shape_ok(h->src.polarization == FDTD_POL_P, h->maps,
+            if (value < 0 || value > 5 || value == 4) break;
+            if (value == 5 && !pair_shape_ok(h->src.polarization == FDTD_POL_P, h->maps,
                                              h->n_labels))
                 break;
             h->opt_variant = (int)value;

@@ -211,6 +211,8 @@ void upload_args(fdtd_batch* b, bool dummy_dft) {
         t.hinc = h->d_hinc; t.einc = h->d_einc; t.phE = h->d_phE; t.phH = h->d_phH;
         t.ez = h->tw_ez; t.hx = h->tw_hx; t.psiE = h->tw_psiE; t.psiH = h->tw_psiH;
         t.dft = h->tw_dft;
+        t.n_tab = table_limit(h);
+        t.dbg = h->d_dbg;
         tw[s] = t;
     }
     BCK(cudaMemcpyAsync(b->d_args, args.data(), args.size() * sizeof(BlockedArgs),
@@ -374,7 +376,6 @@ int fdtd_batch_create(fdtd_handle* const* hs, int32_t n, fdtd_batch** out) {
         configure_twin_batch();
         b->K = std::min(hs[0]->opt_block, blocked_max_K());
         b->variant = hs[0]->opt_variant;
-        if (b->variant == 6) b->variant = 5;      // batches have no capped pair shape
         if (b->variant == 5 && !batch_pair_ok(b)) b->variant = 2;
         *out = b;
         return FDTD_OK;

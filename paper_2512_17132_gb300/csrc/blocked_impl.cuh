@@ -89,6 +89,7 @@ struct Lane {
     const float4* pair;   // code shape 5: label-pair table (shared memory)
     int gx, y0, y1, ny, P, nx;
     bool own, own_r, own_t;
+    bool col_ok;          // the lane's 4 columns lie in [0, nx) (debug index check)
     float S;
 };
 
@@ -107,7 +108,7 @@ __device__ __forceinline__ float4 pair_at(const float4* tab, uint32_t off) {
 // (ca, cb) of column q of a lane from its row's label word.
 // Code shapes that use the label-pair table (S polarisation).
 template <int V>
-constexpr bool kPairShape = (V == 5 || V == 6);
+constexpr bool kPairShape = (V == 5);
 
 template <int V>
 __device__ __forceinline__ float2 coef_s(const Lane& ln, uint32_t w, int q) {
@@ -202,13 +203,16 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
             const int64_t n = n0 + k;
             const float yR = __shfl_down_sync(FULL, p.Y[k][0], 1);
             const bool tf = GENERAL && (r == a.s.js);
-            const float hinc = tf ? a.s.hinc[n] : 0.f;
+            const float hinc = tf ? tab(a.s.hinc, n, a.s) : 0.f;
             const int pe = GENERAL ? pml_e_index(r, ln.ny, ln.P) : -1;
-            if (GENERAL && pe >= 0) {
+            if (GENERAL && pe >= 0 && index_ok(pe < 2 * ln.P, kSitePsiRow, a.s.dbg)) {
                 const float b = a.s.pml_e[pe], c = a.s.pml_e[2 * ln.P + pe];
                 const float ik = a.s.pml_e[4 * ln.P + pe];
                 float psi[4];
-                if (k == 0) ld4(a.psiE_in + (size_t)pe * a.s.pitch + ln.gx, psi);
+                if (k == 0) {
+                    if (ln.col_ok) ld4(a.psiE_in + (size_t)pe * a.s.pitch + ln.gx, psi);
+                    else psi[0] = psi[1] = psi[2] = psi[3] = 0.f;
+                }
                 else {
                     const float4 v = ringE[(r % K) * 32];
                     psi[0] = v.x; psi[1] = v.y; psi[2] = v.z; psi[3] = v.w;
@@ -241,13 +245,16 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
                 }
             }
             if (!GENERAL || r > 0) {
-                const float einc = tf ? a.s.einc[n] : 0.f;
+                const float einc = tf ? tab(a.s.einc, n, a.s) : 0.f;
                 const int ph = GENERAL ? pml_h_index(r, ln.ny, ln.P) : -1;
-                if (GENERAL && ph >= 0) {
+                if (GENERAL && ph >= 0 && index_ok(ph < 2 * ln.P, kSitePsiRow, a.s.dbg)) {
                     const float b = a.s.pml_h[ph], c = a.s.pml_h[2 * ln.P + ph];
                     const float ik = a.s.pml_h[4 * ln.P + ph];
                     float psi[4];
-                    if (k == 0) ld4(a.psiH_in + (size_t)ph * a.s.pitch + ln.gx, psi);
+                    if (k == 0) {
+                        if (ln.col_ok) ld4(a.psiH_in + (size_t)ph * a.s.pitch + ln.gx, psi);
+                        else psi[0] = psi[1] = psi[2] = psi[3] = 0.f;
+                    }
                     else {
                         const float4 v = ringH[(r % K) * 32];
                         psi[0] = v.x; psi[1] = v.y; psi[2] = v.z; psi[3] = v.w;
@@ -298,33 +305,34 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
                     oY[q] = h_new(p.Y[k][q], S, dy);
                 }
             }
-            if (V == 4 && k + 1 < K && ln.own && r >= ln.y0 && r < ln.y1) {
+            if (V == 4 && k + 1 < K && ln.own && r >= ln.y0 && r < ln.y1 &&
+                index_ok(r >= 0 && r < ln.ny && ln.col_ok, kSiteTape, a.s.dbg)) {
                 // code shape 4: the state after step k+1 of this row
                 float* t = a.tape[k] + (size_t)r * a.s.pitch + ln.gx;
                 st4(t, oE);
                 st4(t + a.tape_f, oX);
                 st4(t + 2 * a.tape_f, oY);
             }
-            if (GENERAL && ln.own) {
+            if (GENERAL && ln.own && index_ok(ln.col_ok, kSiteDft, a.s.dbg)) {
                 if (ln.own_r && r == a.s.jr) {
-                    const double2 ph = a.s.phE[n];
+                    const double2 ph = tab(a.s.phE, n, a.s);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) dft_add(&a.s.dft[ln.gx + q], oE[q], ph);
                 }
                 if (ln.own_r && r == a.s.jr + 1) {
-                    const double2 ph = a.s.phH[n];
+                    const double2 ph = tab(a.s.phH, n, a.s);
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
                         dft_add(&a.s.dft[ln.nx + ln.gx + q], hx_avg(p.X[k + 1][q], oX[q]), ph);
                 }
                 if (ln.own_t && r == a.s.jt) {
-                    const double2 ph = a.s.phE[n];
+                    const double2 ph = tab(a.s.phE, n, a.s);
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
                         dft_add(&a.s.dft[2 * ln.nx + ln.gx + q], oE[q], ph);
                 }
                 if (ln.own_t && r == a.s.jt + 1) {
-                    const double2 ph = a.s.phH[n];
+                    const double2 ph = tab(a.s.phH, n, a.s);
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
                         dft_add(&a.s.dft[3 * ln.nx + ln.gx + q], hx_avg(p.X[k + 1][q], oX[q]),
@@ -356,8 +364,7 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
 // that also stores the state after every intermediate step of the launch
 // (its owned rows) into BlockedArgs::tape, for the adjoint's recompute;
 // 5 (S polarisation, at most 16 labels) shape 2 with the label-pair table
-// and paired FP32 instructions on the lean path (advance_lean_pair); 6 shape
-// 5 with one row per trip (built under a register cap, k_blocked_cap168).
+// and paired FP32 instructions on the lean path (advance_lean_pair).
 template <int K, int V, int POL>
 __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float4* s_tab,
                                              const int task, const int64_t n0) {
@@ -377,6 +384,9 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float4*
     const int xg_pre = strip * a.w_int - H + xl;    // global column before wrapping
     ln.gx = ((xg_pre % ln.nx) + ln.nx) % ln.nx;     // nx % 4 == 0: 4 columns stay contiguous
     ln.own = (xl >= H) && (xl < H + a.w_int) && (xg_pre < ln.nx);
+    ln.col_ok = index_ok(ln.gx >= 0 && ln.gx + 4 <= ln.nx && ln.gx % 4 == 0, kSiteRingColumn,
+                         a.s.dbg);
+    ln.own = ln.own && ln.col_ok;      // a lane with bad columns stores nothing
     ln.own_r = (a.s.jr >= ln.y0) && (a.s.jr < ln.y1);
     ln.own_t = (a.s.jt >= ln.y0) && (a.s.jt < ln.y1);
     // CPML carries between levels: psi of a row is written by level k and
@@ -418,7 +428,8 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float4*
 
     auto finish = [&](const int t, float (&fE)[4], float (&fX)[4], float (&fY)[4]) {
         const int ro = t - K;
-        if (ln.own && ro >= y0 && ro < y1) {
+        if (ln.own && ro >= y0 && ro < y1 &&
+            index_ok(ro >= 0 && ro < ny, kSiteStoreRow, a.s.dbg)) {
             const size_t o = (size_t)ro * pitch + ln.gx;
             st4(a.ez_out + o, fE);
             st4(a.hx_out + o, fX);
@@ -432,7 +443,7 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float4*
         __shared__ float4 ring[kRing][3][32];
         __shared__ uint32_t ring_l[kRing][32];
         auto issue = [&](const int row, const int slot) {
-            const bool ok = row >= 0 && row < ny;
+            const bool ok = row >= 0 && row < ny && ln.col_ok;
             const size_t o = (size_t)(ok ? row : 0) * pitch + ln.gx;
             const int nb = ok ? 16 : 0;
             cp_async16(&ring[slot][0][lane], a.ez_in + o, nb);
@@ -450,6 +461,12 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float4*
             float fE[4], fX[4], fY[4];
             const float4 e4 = ring[slot][0][lane], x4 = ring[slot][1][lane], y4 = ring[slot][2][lane];
             uint32_t fL = ring_l[slot][lane];
+            // every label must index the coefficient table (debug builds)
+            index_ok(((fL & 0xffu) < (unsigned)a.s.n_labels) &&
+                         (((fL >> 8) & 0xffu) < (unsigned)a.s.n_labels) &&
+                         (((fL >> 16) & 0xffu) < (unsigned)a.s.n_labels) &&
+                         ((fL >> 24) < (unsigned)a.s.n_labels),
+                     kSiteLabel, a.s.dbg);
             if (kPairShape<V>) fL = pair_offsets(fL);
             fE[0] = e4.x; fE[1] = e4.y; fE[2] = e4.z; fE[3] = e4.w;
             fX[0] = x4.x; fX[1] = x4.y; fX[2] = x4.z; fX[3] = x4.w;
@@ -482,19 +499,22 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float4*
     // software pipeline: row t+1 is fetched while row t is processed
     float nE[4], nX[4], nY[4];
     uint32_t nL = 0u;
-    {
+    if (ln.col_ok && index_ok(t_begin >= 0 && t_begin < ny, kSiteStoreRow, a.s.dbg)) {
         const size_t o = (size_t)t_begin * pitch + ln.gx;
         ld4(a.ez_in + o, nE);
         ld4(a.hx_in + o, nX);
         ld4(a.hy_in + o, nY);
         nL = __ldg(reinterpret_cast<const uint32_t*>(a.s.labels + (size_t)t_begin * lpitch + ln.gx));
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { nE[q] = 0.f; nX[q] = 0.f; nY[q] = 0.f; }
     }
     auto iteration = [&](const int t, const bool fast) {
         float fE[4], fX[4], fY[4];
         uint32_t fL = nL;
 #pragma unroll
         for (int q = 0; q < 4; ++q) { fE[q] = nE[q]; fX[q] = nX[q]; fY[q] = nY[q]; }
-        if (t + 1 < ny) {
+        if (t + 1 < ny && ln.col_ok) {
             const size_t o = (size_t)(t + 1) * pitch + ln.gx;
             ld4(a.ez_in + o, nE);
             ld4(a.hx_in + o, nX);
@@ -565,14 +585,6 @@ template <int K, int POL>
 __global__ void __maxnreg__(224) k_blocked_cap(const BlockedArgs a,
                                                                      const int64_t n0) {
     blocked_kernel_body<K, 3, POL>(a, n0);
-}
-
-// Code shape 6: shape 5 with one row per loop trip, compiled under a
-// 168-register cap, so that 12 one-warp blocks (3 per scheduler) fit an SM;
-// meant for K <= 7 (at K = 8 the cap spills).
-template <int K>
-__global__ void __maxnreg__(168) k_blocked_cap168(const BlockedArgs a, const int64_t n0) {
-    blocked_kernel_body<K, 6, 0>(a, n0);
 }
 
 template <int K, int V, int POL>

@@ -73,6 +73,32 @@ __device__ __forceinline__ void dft_add(double2* acc, float v, double2 ph) {
     *acc = a;
 }
 
+// Index checks of debug builds. Built with FDTD_DEBUG_BOUNDS, the kernels
+// test every global-memory index that is not in range by construction; a
+// failed test sets the bit of its site in the handle's error word and the
+// access is skipped (a load reads 0), so the kernel finishes and the host
+// reports FDTD_EBOUNDS. Release builds compile the tests away.
+enum CheckSite : unsigned {
+    kSiteRingColumn = 0,   // blocked: lane columns of a level-0 row load
+    kSiteStoreRow = 1,     // blocked: row and columns of a stored row
+    kSitePsiRow = 2,       // CPML carry row index
+    kSiteTable = 3,        // incident / phase table entry (step index)
+    kSiteDft = 4,          // monitor accumulator column
+    kSiteLabel = 5,        // label value against the coefficient table
+    kSiteTape = 6,         // adjoint tape row
+    kSiteTask = 7,         // warp task / segment index
+};
+
+__device__ __forceinline__ bool index_ok(bool ok, unsigned site, unsigned* err) {
+#ifdef FDTD_DEBUG_BOUNDS
+    if (!ok && err) atomicOr(err, 1u << site);
+    return ok;
+#else
+    (void)site; (void)err;
+    return true;
+#endif
+}
+
 // Arguments common to the field-update kernels.
 struct StepArgs {
     int nx, ny;
@@ -93,7 +119,28 @@ struct StepArgs {
     const double2* phE;   // e^{i w0 (n+1/2) dt}
     const double2* phH;   // e^{i w0 (n+1) dt}
     double2* dft;         // [4][nx]: Ez(jr), Hx(jr), Ez(jt), Hx(jt)
+    int64_t n_tab;        // table entries valid on the device (debug index checks)
+    int n_coef;           // entries of coef (debug index checks)
+    unsigned* dbg;        // error word of the debug index checks (null: none)
 };
+
+// Table entry n of the incident / phase tables of n_tab entries; debug
+// builds check n.
+template <typename T>
+__device__ __forceinline__ T tab_n(const T* t, int64_t n, int64_t n_tab, unsigned* dbg) {
+    return index_ok(n >= 0 && n < n_tab, kSiteTable, dbg) ? t[n] : T{};
+}
+template <typename T>
+__device__ __forceinline__ T tab(const T* t, int64_t n, const StepArgs& s) {
+    return tab_n(t, n, s.n_tab, s.dbg);
+}
+
+// Coefficients of a label (S: per label, P: per label pair); debug builds
+// check the index against the table.
+__device__ __forceinline__ float2 coef_at(const StepArgs& s, int idx) {
+    return index_ok(idx >= 0 && idx < s.n_coef, kSiteLabel, s.dbg) ? s.coef[idx]
+                                                                    : make_float2(0.f, 0.f);
+}
 
 // Index of a CPML row within the [2P] tables and psi arrays, or -1.
 __device__ __forceinline__ int pml_e_index(int j, int ny, int P) {

@@ -95,6 +95,8 @@ struct TwinArgs {
     const double2* phE; const double2* phH;
     float* ez; float* hx; float* psiE; float* psiH;
     double2* dft;         // [4]: Ez(jr), Hx(jr), Ez(jt), Hx(jt)
+    int64_t n_tab;        // table entries valid on the device (debug index checks)
+    unsigned* dbg;        // error word of the debug index checks (null: none)
 };
 
 struct BlockPlan;
@@ -132,6 +134,17 @@ struct Fail {
     int code;
 };
 StepArgs step_args(fdtd_handle* h);
+// table entries that kernels of this handle may read (the debug checks'
+// bound); debug builds can lower it to exercise the checks
+int64_t table_limit(const fdtd_handle* h);
+// Debug builds: every dalloc'd buffer sits between two guard bands of
+// kGuardBytes filled with kGuardByte; these check the bands and the index
+// error word, and fail with FDTD_EBOUNDS naming what they found.
+constexpr size_t kGuardBytes = 256;
+constexpr unsigned char kGuardByte = 0xA5;
+void debug_checks(fdtd_handle* h);
+void launch_guard_check(const unsigned char* p, size_t n, unsigned char want, unsigned* flag,
+                        unsigned bit, cudaStream_t st);
 void ensure_tables(fdtd_handle* h, int64_t n_end);
 void produce_tables(fdtd_handle* h, int64_t upto);
 void compute_tables(fdtd_handle* h, int64_t upto);
@@ -184,6 +197,9 @@ struct fdtd_handle {
     double* d_flux = nullptr;
     double* h_flux = nullptr;  // pinned
     int* d_flag = nullptr;
+    unsigned* d_dbg = nullptr;   // error word of the debug index checks
+    std::vector<void*> guarded;  // debug builds: this handle's guarded buffers
+    int64_t dbg_tab_limit = 0;   // debug builds: table entries the checks admit (0: all)
     // incident-wave and phase tables (absolute step index)
     std::shared_ptr<fdtd::TableStore> tables;
     int64_t tab_plan = 0;       // steps the buffers are planned for

@@ -2,6 +2,8 @@
 // reduction and the field pack/unpack kernels.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "fdtd_internal.h"
 
 namespace fdtd {
@@ -20,9 +22,9 @@ __global__ void k_naive_e(StepArgs a, float* __restrict__ ez, const float* __res
     const float dhy = __fsub_rn(hy[(size_t)j * a.pitch + ir], hy[o]);
     const float hxb = (j + 1 < a.ny) ? hx[o + a.pitch] : 0.0f;         // Hx[ny] = 0
     float dhx = __fsub_rn(hxb, hx[o]);
-    if (j == a.js) dhx = __fsub_rn(dhx, a.hinc[n]);                    // TF cell sees total Hx
+    if (j == a.js) dhx = __fsub_rn(dhx, tab(a.hinc, n, a));            // TF cell sees total Hx
     float2 c;
-    if (POL == 0) c = a.cellcoef ? a.cellcoef[o] : a.coef[a.labels[(size_t)j * a.lpitch + i]];
+    if (POL == 0) c = a.cellcoef ? a.cellcoef[o] : coef_at(a, a.labels[(size_t)j * a.lpitch + i]);
     else c = make_float2(1.0f, a.S);
     const float e = ez[o];
     const int pj = pml_e_index(j, a.ny, a.P);
@@ -53,14 +55,14 @@ __global__ void k_naive_h(StepArgs a, const float* __restrict__ ez, float* __res
     if (POL == 0) {
         hy[o] = h_new(hy[o], a.S, __fsub_rn(e, ez[(size_t)j * a.pitch + il]));
     } else {
-        const float2 cy = a.coef[pair_index(a.labels[lo + il], a.labels[lo + i])];
+        const float2 cy = coef_at(a, pair_index(a.labels[lo + il], a.labels[lo + i]));
         hy[o] = e_edge_new(cy.x, cy.y, hy[o], __fsub_rn(e, ez[(size_t)j * a.pitch + il]));
     }
     if (j > 0) {
         float d = __fsub_rn(e, ez[o - a.pitch]);
-        if (j == a.js) d = __fsub_rn(d, a.einc[n]);                    // SF edge sees scattered Ez
+        if (j == a.js) d = __fsub_rn(d, tab(a.einc, n, a));            // SF edge sees scattered Ez
         float2 cx = make_float2(1.0f, a.S);
-        if (POL == 1) cx = a.coef[pair_index(a.labels[lo - a.lpitch + i], a.labels[lo + i])];
+        if (POL == 1) cx = coef_at(a, pair_index(a.labels[lo - a.lpitch + i], a.labels[lo + i]));
         const int pj = pml_h_index(j, a.ny, a.P);
         if (pj >= 0) {
             const float b = a.pml_h[pj], cc = a.pml_h[2 * a.P + pj], ik = a.pml_h[4 * a.P + pj];
@@ -84,8 +86,9 @@ __global__ void k_naive_dft(StepArgs a, const float* __restrict__ ez,
     const int w = blockIdx.y;
     const int row = w ? a.jt : a.jr;
     const size_t o = (size_t)row * a.pitch + i;
-    dft_add(&a.dft[(size_t)(2 * w) * a.nx + i], ez[o], a.phE[n]);
-    dft_add(&a.dft[(size_t)(2 * w + 1) * a.nx + i], hx_avg(hx[o], hx[o + a.pitch]), a.phH[n]);
+    dft_add(&a.dft[(size_t)(2 * w) * a.nx + i], ez[o], tab(a.phE, n, a));
+    dft_add(&a.dft[(size_t)(2 * w + 1) * a.nx + i], hx_avg(hx[o], hx[o + a.pitch]),
+            tab(a.phH, n, a));
 }
 
 void launch_naive_step(const StepArgs& a, float* ez, float* hx, float* hy, float* psiE,
@@ -109,7 +112,7 @@ __device__ __forceinline__ void twin_column_global(const TwinArgs& a, int64_t n0
     const int ny = a.ny;
     for (int s = 0; s < steps; ++s) {
         const int64_t n = n0 + s;
-        const float hinc = a.hinc[n], einc = a.einc[n];
+        const float hinc = tab_n(a.hinc, n, a.n_tab, a.dbg), einc = tab_n(a.einc, n, a.n_tab, a.dbg);
         for (int j = threadIdx.x; j < ny; j += blockDim.x) {
             const float hxb = (j + 1 < ny) ? a.hx[j + 1] : 0.0f;
             float dhx = __fsub_rn(hxb, a.hx[j]);
@@ -126,8 +129,8 @@ __device__ __forceinline__ void twin_column_global(const TwinArgs& a, int64_t n0
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            dft_add(&a.dft[0], a.ez[a.jr], a.phE[n]);
-            dft_add(&a.dft[2], a.ez[a.jt], a.phE[n]);
+            dft_add(&a.dft[0], a.ez[a.jr], tab_n(a.phE, n, a.n_tab, a.dbg));
+            dft_add(&a.dft[2], a.ez[a.jt], tab_n(a.phE, n, a.n_tab, a.dbg));
         }
         for (int j = threadIdx.x + 1; j < ny; j += blockDim.x) {
             float d = __fsub_rn(a.ez[j], a.ez[j - 1]);
@@ -143,8 +146,8 @@ __device__ __forceinline__ void twin_column_global(const TwinArgs& a, int64_t n0
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            dft_add(&a.dft[1], hx_avg(a.hx[a.jr], a.hx[a.jr + 1]), a.phH[n]);
-            dft_add(&a.dft[3], hx_avg(a.hx[a.jt], a.hx[a.jt + 1]), a.phH[n]);
+            dft_add(&a.dft[1], hx_avg(a.hx[a.jr], a.hx[a.jr + 1]), tab_n(a.phH, n, a.n_tab, a.dbg));
+            dft_add(&a.dft[3], hx_avg(a.hx[a.jt], a.hx[a.jt + 1]), tab_n(a.phH, n, a.n_tab, a.dbg));
         }
     }
 }
@@ -169,7 +172,7 @@ __device__ __forceinline__ void twin_column_smem(const TwinArgs& a, int64_t n0, 
     __syncthreads();
     for (int s = 0; s < steps; ++s) {
         const int64_t n = n0 + s;
-        const float hinc = a.hinc[n], einc = a.einc[n];
+        const float hinc = tab_n(a.hinc, n, a.n_tab, a.dbg), einc = tab_n(a.einc, n, a.n_tab, a.dbg);
         for (int j = threadIdx.x; j < ny; j += blockDim.x) {
             const float hxb = (j + 1 < ny) ? hx[j + 1] : 0.0f;
             float dhx = __fsub_rn(hxb, hx[j]);
@@ -186,8 +189,8 @@ __device__ __forceinline__ void twin_column_smem(const TwinArgs& a, int64_t n0, 
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            dft_add(&d0, ez[a.jr], a.phE[n]);
-            dft_add(&d2, ez[a.jt], a.phE[n]);
+            dft_add(&d0, ez[a.jr], tab_n(a.phE, n, a.n_tab, a.dbg));
+            dft_add(&d2, ez[a.jt], tab_n(a.phE, n, a.n_tab, a.dbg));
         }
         for (int j = threadIdx.x + 1; j < ny; j += blockDim.x) {
             float d = __fsub_rn(ez[j], ez[j - 1]);
@@ -203,8 +206,8 @@ __device__ __forceinline__ void twin_column_smem(const TwinArgs& a, int64_t n0, 
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            dft_add(&d1, hx_avg(hx[a.jr], hx[a.jr + 1]), a.phH[n]);
-            dft_add(&d3, hx_avg(hx[a.jt], hx[a.jt + 1]), a.phH[n]);
+            dft_add(&d1, hx_avg(hx[a.jr], hx[a.jr + 1]), tab_n(a.phH, n, a.n_tab, a.dbg));
+            dft_add(&d3, hx_avg(hx[a.jt], hx[a.jt + 1]), tab_n(a.phH, n, a.n_tab, a.dbg));
         }
     }
     __syncthreads();
@@ -407,6 +410,24 @@ __global__ void k_check_finite(const float* __restrict__ p, int pitch, int nx, i
 void launch_check_finite(const float* p, int pitch, int nx, int ny, int* flag,
                          cudaStream_t st) {
     k_check_finite<<<dim3((nx + 255) / 256, ny), 256, 0, st>>>(p, pitch, nx, ny, flag);
+}
+
+// Debug builds: bytes [p, p + n) must all equal `want` (a guard band);
+// otherwise bit `bit` of *flag is set.
+__global__ void k_guard_check(const unsigned char* p, size_t n, unsigned char want,
+                              unsigned* flag, unsigned bit) {
+    bool bad = false;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        bad |= (p[i] != want);
+    if (bad) atomicOr(flag, 1u << bit);
+}
+
+void launch_guard_check(const unsigned char* p, size_t n, unsigned char want, unsigned* flag,
+                        unsigned bit, cudaStream_t st) {
+    if (n == 0) return;
+    const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 64);
+    k_guard_check<<<blocks, 256, 0, st>>>(p, n, want, flag, bit);
 }
 
 }  // namespace fdtd

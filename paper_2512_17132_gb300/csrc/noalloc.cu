@@ -249,6 +249,8 @@ extern "C" int fdtd_blocked_advance_noalloc(const fdtd_grid* grid, const uint8_t
     a.s.phE = reinterpret_cast<const double2*>(sb + off_tab + 16 * sizeof(float));
     a.s.phH = reinterpret_cast<const double2*>(sb + off_tab + 16 * sizeof(float) + 8 * sizeof(double2));
     a.s.dft = reinterpret_cast<double2*>(sb + off_dft);
+    a.s.n_tab = 8;                 // the zeroed source tables hold 8 steps
+    a.s.n_coef = n_labels;
     a.ez_in = in[0]; a.hx_in = in[1]; a.hy_in = in[2];
     a.psiE_in = in[3]; a.psiH_in = in[4];
     a.ez_out = out[0]; a.hx_out = out[1]; a.hy_out = out[2];

@@ -10,13 +10,16 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libfdtd.so")
+# FDTD_LIB selects another build of the library (the debug build for the
+# index-check tests); the default is the release build next to this file
+LIB_PATH = os.environ.get("FDTD_LIB") or os.path.join(HERE, "libfdtd.so")
 
 FDTD_OK, FDTD_EINVAL, FDTD_ENOMEM, FDTD_ECUDA = 0, -1, -2, -3
-FDTD_EUNSTABLE, FDTD_ETIMEOUT, FDTD_ESTATE = -4, -5, -6
+FDTD_EUNSTABLE, FDTD_EBOUNDS, FDTD_ESTATE = -4, -5, -6
 FDTD_OPT_KERNEL, FDTD_OPT_BLOCK_STEPS, FDTD_OPT_SEG_ROWS = 1, 2, 3
 FDTD_OPT_TIMING, FDTD_OPT_WATCHDOG, FDTD_OPT_VARIANT, FDTD_OPT_GRAPH = 4, 5, 6, 7
 FDTD_OPT_PLAN_WEIGHT = 8
+FDTD_OPT_DEBUG_TABLE_LIMIT, FDTD_OPT_DEBUG_POKE_GUARD = 9, 10
 FDTD_POL_S, FDTD_POL_P = 0, 1
 KERNEL_AUTO, KERNEL_NAIVE, KERNEL_BLOCKED = 0, 1, 2
 

@@ -11,6 +11,10 @@ and bench.py compare the CUDA library with these files.
       config 3 (healthy monocot, 550 nm, dx = 15 nm) cropped to its first
       8192 rows (the whole leaf and both monitors) and 2048 columns, with R, T
       and the DFT lines after 4000 and after 60 000 steps.
+  python tests/golden/make_oracle_goldens.py e2 [--threads N]
+      the validation cylinder array of Sec. 3 (100 x 897 cells, h = 0.01 m),
+      60 000 steps, S and P polarisation, at L/lambda = 0.75, 0.82, 0.855
+      and 0.90 (the P runs use the numpy TEz oracle).
 
 Each run writes oracle_<case>.json (scalars, with the command that made
 them) and oracle_<case>.npz (the four DFT lines, complex128, in the order
@@ -31,7 +35,8 @@ ROOT = os.path.dirname(os.path.dirname(HERE))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-from fdtd_inputs import config_c2, config_c3, crop_layout  # noqa: E402
+from fdtd_inputs import config_c2, config_c3, config_e2, crop_layout  # noqa: E402
+from oracle.fdtd_tez import TEzOracle, empty_twin_tez  # noqa: E402
 from oracle.fdtd_tmz import empty_twin  # noqa: E402
 from oracle.fdtd_tmz_c import TMzOracleC  # noqa: E402
 
@@ -59,7 +64,8 @@ def _record(name, spec, leaf, twin, steps, wall, threads, cmd, extra=None):
     rec = dict(
         case=name, nx=spec.nx, ny=spec.ny, dx=spec.dx, dt=spec.dt, steps=int(steps),
         lambda0=spec.lambda0, r_row=spec.r_row, t_row=spec.t_row, tfsf_row=spec.tfsf_row,
-        polarization="S (TMz)", R=ratio(p_up), T=ratio(p_down),
+        polarization="P (TEz)" if getattr(spec, "polarization", 0) else "S (TMz)",
+        R=ratio(p_up), T=ratio(p_down),
         A=None if p_inc <= 0.0 else 1.0 - (p_up + p_down) / p_inc, p_up=p_up, p_down=p_down, p_inc=p_inc,
         oracle="FP64 oracle (TMzOracle state, C time loop TMzOracleC)",
         threads=int(threads), wall_s=round(wall, 1), command=cmd)
@@ -67,11 +73,12 @@ def _record(name, spec, leaf, twin, steps, wall, threads, cmd, extra=None):
         rec.update(extra)
     idx = sample_index(spec.ny, spec.nx)
     d = leaf.dft
+    fields = leaf.fields()                   # (Ez, Hx, Hy) or, for P, (Hz, Ex, Ey)
     np.savez_compressed(
         os.path.join(HERE, f"oracle_{name}.npz"),
         dft=np.stack([d["e_r"], d["h_r"], d["e_t"], d["h_t"]]),
-        idx=idx, ez=leaf.ez.ravel()[idx], hx=leaf.hx.ravel()[idx], hy=leaf.hy.ravel()[idx],
-        max_abs=np.array([np.abs(leaf.ez).max(), np.abs(leaf.hx).max(), np.abs(leaf.hy).max()]))
+        idx=idx, ez=fields[0].ravel()[idx], hx=fields[1].ravel()[idx],
+        hy=fields[2].ravel()[idx], max_abs=np.array([np.abs(f).max() for f in fields]))
     with open(os.path.join(HERE, f"oracle_{name}.json"), "w") as f:
         json.dump(rec, f, indent=1)
     print(json.dumps({k: rec[k] for k in ("case", "steps", "R", "T", "A", "wall_s")}), flush=True)
@@ -102,6 +109,26 @@ def run_c3crop(threads):
                 dict(seed=0, crop="config 3 healthy, rows 0-8191, columns 0-2047"))
 
 
+E2_POINTS = (0.75, 0.82, 0.855, 0.90)
+
+
+def run_e2(threads):
+    for pol in (0, 1):
+        for x in E2_POINTS:
+            spec = config_e2(x, steps=60000).with_(polarization=pol)
+            t = time.time()
+            if pol:
+                leaf = TEzOracle(spec).run(spec.steps)
+                twin = empty_twin_tez(spec).run(spec.steps)
+            else:
+                leaf = TMzOracleC(spec).run(spec.steps, threads)
+                twin = empty_twin(spec).run(spec.steps)
+            _record(f"e2_{'SP'[pol]}_{x:g}", spec, leaf, twin, spec.steps, time.time() - t,
+                    threads if not pol else 1,
+                    f"python tests/golden/make_oracle_goldens.py e2 --threads {threads}",
+                    dict(l_over_lambda=x))
+
+
 def main(argv):
     threads = os.cpu_count() or 1
     if "--threads" in argv:
@@ -114,6 +141,8 @@ def main(argv):
             run_c2(float(lam), threads)
     elif case == "c3crop":
         run_c3crop(threads)
+    elif case == "e2":
+        run_e2(threads)
     else:
         raise SystemExit(__doc__)
 

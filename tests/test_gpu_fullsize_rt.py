@@ -9,14 +9,16 @@ only the oracle (its C time loop, bit-identical to the numpy loop):
 * config 3: the healthy monocot at 550 nm cropped to 8192 x 2048 cells (the
   whole leaf and both monitors), after 4000 and after 60 000 steps.
 
-Bounds. R and T: 2e-3 absolute (the parity requirement of the scope). The
+Bounds. R and T: 2e-3 absolute (the parity requirement of the scope); the
+first config-2 comparison measured 3e-7 and 9e-8 (550 nm). The
 DFT lines and the fields at 4096 sampled cells carry the FP32 rounding of
 the whole run: each step rounds every field to 2^-24 relative and the
 errors of independent cells add up like a random walk over the steps and
 over the cells a wave crosses, sqrt(30 000) x 6e-8 ~ 1e-5, amplified by the
 resonances of the cross-section. The tests bound the DFT lines at 1e-3 of
 their largest value and the sampled fields at 1e-3 relative L2, and print
-what they measure.
+what they measure (about 2e-5 and 3e-5 at 550 nm). A monitor line the
+pulse has not reached yet is zero in both and must be exactly zero.
 """
 import glob
 import json
@@ -69,8 +71,14 @@ def _compare(sim, rec, ref, name):
     d = sim.dft()
     ez, hx, hy = sim.fields()
     idx = ref["idx"]
-    line_err = [float(np.abs(d[q] - ref["dft"][q]).max() / np.abs(ref["dft"][q]).max())
-                for q in range(4)]
+    line_err = []
+    for q in range(4):
+        scale = np.abs(ref["dft"][q]).max()
+        if scale == 0.0:
+            # the pulse has not reached this monitor: both lines are exactly zero
+            assert np.all(d[q] == 0.0), name
+            continue
+        line_err.append(float(np.abs(d[q] - ref["dft"][q]).max() / scale))
     # E and eta0 H have the same scale
     g = np.concatenate([ez.ravel()[idx], hx.ravel()[idx] * ETA0, hy.ravel()[idx] * ETA0])
     r = np.concatenate([ref["ez"], ref["hx"] * ETA0, ref["hy"] * ETA0])
