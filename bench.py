@@ -58,6 +58,9 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-adjoint", action="store_true",
                    help="skip the config-5 adjoint pass of the default line")
+    p.add_argument("--adj-block", type=int, default=-1,
+                   help="reverse steps per adjoint launch (0: one per step; default: the "
+                        "library's)")
     p.add_argument("--pol", default="s", choices=["s", "p"],
                    help="polarisation of the runs: s (TMz, the default) or p (TEz)")
     return p.parse_args()
@@ -381,7 +384,7 @@ def golden_rt_check(results, steps):
             "bound": 2e-3}
 
 
-def adjoint_pass(fdtd, torch):
+def adjoint_pass(fdtd, torch, adj_block=-1):
     """One config-5 gradient pass (1000 x 6000 cells, 30 000 steps,
     checkpoints every 500): the checkpointed forward and the discrete
     adjoint of R(550 nm), each timed with the CUDA-synchronised wall clock
@@ -391,6 +394,8 @@ def adjoint_pass(fdtd, torch):
     spec = fi.config_c5()
     cells = spec.nx * spec.ny * spec.steps
     with fdtd.Simulation(spec) as sim:
+        if adj_block >= 0:
+            fdtd.fdtd_set_option(sim.h, fdtd.FDTD_OPT_ADJ_BLOCK, adj_block)
         fdtd.fdtd_forward_checkpointed(sim.h, 2000, 500)          # warm-up
         fdtd.fdtd_backward(sim.h, 1.0, 0.0, spec.ny, spec.nx, len(spec.materials))
         torch.cuda.synchronize()
@@ -614,6 +619,8 @@ def run_c5(args):
     spec = fi.config_c5(steps=args.fdtd_steps or 30000)
     cells = spec.nx * spec.ny * spec.steps
     sim = fdtd.Simulation(spec)
+    if args.adj_block >= 0:
+        fdtd.fdtd_set_option(sim.h, fdtd.FDTD_OPT_ADJ_BLOCK, args.adj_block)
     fdtd.fdtd_forward_checkpointed(sim.h, min(2000, spec.steps), 500)   # warm-up
     fdtd.fdtd_backward(sim.h, 1.0, 0.0, spec.ny, spec.nx, len(spec.materials))
     clocks = ClockSampler(_device_id())
@@ -779,7 +786,7 @@ def main():
 
     adjoint = None
     if rank == 0 and world == 1 and not args.no_adjoint and args.pol == "s":
-        adjoint = adjoint_pass(fdtd, torch)
+        adjoint = adjoint_pass(fdtd, torch, args.adj_block)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

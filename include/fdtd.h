@@ -146,6 +146,11 @@ typedef struct fdtd_stats {
 #define FDTD_OPT_PLAN_WEIGHT 8 /* segment planner: cost of a general-path iteration of the blocked
                                   kernel in lean iterations, times 1000 (0: the measured default,
                                   12 for S and 7.5 for P); batches take each handle's value */
+#define FDTD_OPT_ADJ_BLOCK 11    /* fdtd_backward: reverse steps per launch of the temporally
+                                  blocked reverse kernel, 1..4 (default 4), or 0 for one launch
+                                  pair per reverse step; labelled handles with nx % 4 == 0 (the
+                                  others always take one step per launch); same gradients bit
+                                  for bit */
 #define FDTD_OPT_DEBUG_TABLE_LIMIT 9 /* debug builds only (else FDTD_EINVAL): the index checks
                                   admit only this many incident/phase table entries (0: all
                                   allocated), so a longer run trips the table check without

@@ -478,6 +478,349 @@ __global__ void k_adj_chain(ChainArgs a) {
             if (s_lab[t] != 0.0) atomicAdd(&a.g_lab[t], s_lab[t]);
 }
 
+// ---------------------------------------------------------------------------
+// Temporally blocked reverse steps (labelled handles, nx % 4 == 0): K reverse
+// steps n_top, n_top - 1, ..., n_top - K + 1 in one launch. The reverse step
+// has the one-row reach of the forward step in both directions (the
+// transpose of the H update looks one row down, that of the E update one row
+// up), so the forward kernel's pipeline carries over: a warp owns a strip of
+// 128 columns and a segment of rows, streams down the rows once, and level k
+// (reverse step n_top - k) produces its output row r = t - k - 1 at
+// iteration t from its input rows r and r + 1. Only level 0's input (the
+// adjoint state lE, lX, lY) is read from memory and only level K's output
+// written; the adjoint CPML carries travel between levels in a per-warp
+// shared-memory ring; every level reads the taped forward state of its step
+// (Ez, Hy of row r, Hx of row r + 1; Hx of row r is kept from the previous
+// iteration). Each cell's gradient sums are read, updated and written by
+// the one lane that owns it, level after level, so they accumulate in the
+// same order as with one reverse step per launch. Every expression is that
+// of k_adj_h4 / k_adj_e4, so the gradients are bit for bit the same.
+struct AdjBlockArgs {
+    AdjArgs a;                          // lE, lX, lY, tE.. unused here
+    const float* lE_in; const float* lX_in; const float* lY_in;
+    float* lE_out; float* lX_out; float* lY_out;
+    const float* mE_in; const float* mH_in;
+    float* mE_out; float* mH_out;
+    float* const* tape;                 // tape state base pointers; level k uses tape[m_top - k]
+    int m_top;
+    size_t tape_f;                      // floats per field of a tape state (pitch * ny)
+    const int* seg_y0;
+    int n_strips, n_tasks, w_int;
+};
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ void ld4g(const float* p, float (&v)[4]) {
+    const float4 x = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+}
+__device__ __forceinline__ void ld4c(const float* p, float (&v)[4]) {   // written in this kernel
+    const float4 x = *reinterpret_cast<const float4*>(p);
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+}
+__device__ __forceinline__ void st4g(float* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+// Per-level pipeline registers: the level's pending input row r (lE, lX,
+// lY and its label word), adj_dez of row r, g0 (the E-transpose term) of row
+// r - 1, and the taped Hx of row r.
+template <int K>
+struct AdjPipe {
+    float E[K][4], X[K][4], Y[K][4], D[K][4], G[K][4], TX[K][4];
+    uint32_t L[K];
+};
+
+struct AdjLane {
+    int gx, y0, y1, nx, ny, P;
+    bool own;
+};
+
+// One level of one iteration: reverse step n = n_top - k turns the level's
+// input rows r = q - 1 (pending) and q (iE, iX, iY, iL) into its output row
+// r, returned in iE, iX, iY, iL as the input row of level k + 1. GENERAL is
+// the path for iterations that touch a CPML, source, monitor or boundary
+// row; both paths round identically.
+template <int K, bool GENERAL>
+__device__ __forceinline__ void adj_level(const AdjBlockArgs& b, const float2* s_coef,
+                                          AdjPipe<K>& p, const int k, const int t,
+                                          const int64_t n_top, const float* tb, float (&iE)[4],
+                                          float (&iX)[4], float (&iY)[4], uint32_t& iL,
+                                          const AdjLane& ln, float4* ringE, float4* ringH) {
+    const AdjArgs& a = b.a;
+    const int q = t - k, r = q - 1;
+    const int64_t n = n_top - k;
+    const float S = a.S;
+    const size_t pitch = (size_t)a.pitch;
+    const bool r_ok = !GENERAL || (r >= 0 && r < ln.ny);
+    // taped forward state of step n: Ez, Hy of row r, Hx of row q
+    float tE[4], tY[4], tXq[4];
+    if (r_ok && index_ok(!GENERAL || (r >= 0 && r < ln.ny), kSiteTape, a.dbg)) {
+        ld4g(tb + (size_t)r * pitch + ln.gx, tE);
+        ld4g(tb + 2 * b.tape_f + (size_t)r * pitch + ln.gx, tY);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) { tE[c] = 0.f; tY[c] = 0.f; }
+    }
+    if (!GENERAL || (q >= 0 && q < ln.ny)) {
+        ld4g(tb + b.tape_f + (size_t)q * pitch + ln.gx, tXq);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) tXq[c] = 0.f;        // Hx[ny] = 0
+    }
+    // 1. transpose of the Hx update at edge q (adj_dez), psi_H carry of row q
+    float dq[4];
+    if (!GENERAL) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) dq[c] = __fmul_rn(S, iX[c]);
+    } else if (q <= 0 || q >= ln.ny) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) dq[c] = 0.f;
+    } else {
+        float x[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) x[c] = iX[c];
+        if (q == a.jr || q == a.jr + 1 || q == a.jt || q == a.jt + 1)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) x[c] = __fadd_rn(x[c], src_h(a, q, ln.gx + c, n));
+        const int ph = pml_h_index(q, ln.ny, ln.P);
+        if (ph >= 0 && index_ok(ph < 2 * ln.P, kSitePsiRow, a.dbg)) {
+            const float bb = a.pml_h[ph], cc = a.pml_h[2 * a.P + ph], ik = a.pml_h[4 * a.P + ph];
+            float m[4], mo[4];
+            if (k == 0) {
+                ld4g(b.mH_in + (size_t)ph * pitch + ln.gx, m);
+            } else {
+                const float4 v = ringH[(q % K) * 32];
+                m[0] = v.x; m[1] = v.y; m[2] = v.z; m[3] = v.w;
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float sx = __fmul_rn(S, x[c]);
+                const float nu = __fadd_rn(sx, m[c]);
+                mo[c] = __fmul_rn(bb, nu);
+                dq[c] = __fmaf_rn(cc, nu, __fmul_rn(sx, ik));
+            }
+            if (k == K - 1) {
+                if (ln.own && q >= ln.y0 && q < ln.y1) st4g(b.mH_out + (size_t)ph * pitch + ln.gx, mo);
+            } else {
+                ringH[(q % K) * 32] = make_float4(mo[0], mo[1], mo[2], mo[3]);
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) dq[c] = __fmul_rn(S, x[c]);
+        }
+    }
+    float oE[4], oX[4], oY[4], g0[4];
+    if (r_ok) {
+        // 2. the adjoint of Ez^{n+1/2} after the H transposes (k_adj_h)
+        const float yR = __shfl_down_sync(kFull, p.Y[k][0], 1);
+        float eh[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            eh[c] = __fadd_rn(p.E[k][c], __fmul_rn(S, __fsub_rn(p.Y[k][c], c < 3 ? p.Y[k][c + 1] : yR)));
+            eh[c] = __fadd_rn(eh[c], __fsub_rn(p.D[k][c], dq[c]));
+        }
+        if (GENERAL && (r == a.jr || r == a.jt))
+#pragma unroll
+            for (int c = 0; c < 4; ++c) eh[c] = __fadd_rn(eh[c], src_e(a, r, ln.gx + c, n));
+        // 3. the forward curl of step n from the tape (forward rounding)
+        const float tyR = __shfl_down_sync(kFull, tY[0], 1);
+        float curl[4];
+        const int pe = GENERAL ? pml_e_index(r, ln.ny, ln.P) : -1;
+        float psi_old[4];
+        if (GENERAL && pe >= 0) ld4g(tb + 3 * b.tape_f + (size_t)pe * pitch + ln.gx, psi_old);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float dhy = __fsub_rn(c < 3 ? tY[c + 1] : tyR, tY[c]);
+            float dhx = __fsub_rn(tXq[c], p.TX[k][c]);
+            if (GENERAL && r == a.js) dhx = __fsub_rn(dhx, tab_n(a.hinc, n, a.n_tab, a.dbg));
+            if (GENERAL && pe >= 0) {
+                const float bb = a.pml_e[pe], cc = a.pml_e[2 * a.P + pe], ik = a.pml_e[4 * a.P + pe];
+                const float psi = psi_new(bb, cc, psi_old[c], dhx);
+                curl[c] = __fadd_rn(dhy, __fmaf_rn(dhx, ik, psi));
+            } else {
+                curl[c] = __fadd_rn(dhy, dhx);
+            }
+        }
+        // 4. gradient sums of the owned cells (one lane per cell, level order = step order)
+        if (ln.own && r >= ln.y0 && r < ln.y1) {
+            const size_t o = (size_t)r * pitch + ln.gx;
+            float gA[4], gB[4];
+            ld4c(a.gA + o, gA);
+            ld4c(a.gB + o, gB);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                gA[c] = __fmaf_rn(eh[c], tE[c], gA[c]);
+                gB[c] = __fmaf_rn(eh[c], curl[c], gB[c]);
+            }
+            st4g(a.gA + o, gA);
+            st4g(a.gB + o, gB);
+        }
+        // 5. transpose of the Ez update (adj_curl of row r), psi_E carry of row r
+        const uint32_t L = p.L[k];
+        float2 cf[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) cf[c] = s_coef[(L >> (8 * c)) & 0xffu];
+        float cbar[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) cbar[c] = __fmul_rn(cf[c].y, eh[c]);
+        if (GENERAL && pe >= 0 && index_ok(pe < 2 * ln.P, kSitePsiRow, a.dbg)) {
+            const float bb = a.pml_e[pe], cc = a.pml_e[2 * a.P + pe], ik = a.pml_e[4 * a.P + pe];
+            float m[4], mo[4];
+            if (k == 0) {
+                ld4g(b.mE_in + (size_t)pe * pitch + ln.gx, m);
+            } else {
+                const float4 v = ringE[(r % K) * 32];
+                m[0] = v.x; m[1] = v.y; m[2] = v.z; m[3] = v.w;
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float rho = __fadd_rn(cbar[c], m[c]);
+                mo[c] = __fmul_rn(bb, rho);
+                g0[c] = __fmaf_rn(cc, rho, __fmul_rn(cbar[c], ik));
+            }
+            if (k == K - 1) {
+                if (ln.own && r >= ln.y0 && r < ln.y1) st4g(b.mE_out + (size_t)pe * pitch + ln.gx, mo);
+            } else {
+                ringE[(r % K) * 32] = make_float4(mo[0], mo[1], mo[2], mo[3]);
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) g0[c] = cbar[c];
+        }
+        const float cl0 = __shfl_up_sync(kFull, cbar[3], 1);
+        const bool mon = GENERAL && (r == a.jr || r == a.jr + 1 || r == a.jt || r == a.jt + 1);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float cl = c ? cbar[c - 1] : cl0;
+            const float gu = (GENERAL && r == 0) ? 0.f : p.G[k][c];
+            oY[c] = __fadd_rn(p.Y[k][c], __fsub_rn(cl, cbar[c]));
+            float x = p.X[k][c];
+            if (mon) x = __fadd_rn(x, src_h(a, r, ln.gx + c, n));
+            oX[c] = __fadd_rn(x, __fsub_rn(gu, g0[c]));
+            oE[c] = __fmul_rn(cf[c].x, eh[c]);
+        }
+    } else {
+        // outside the grid (warp-uniform): a zero row, which reaches no stored row
+#pragma unroll
+        for (int c = 0; c < 4; ++c) { oE[c] = 0.f; oX[c] = 0.f; oY[c] = 0.f; g0[c] = 0.f; }
+    }
+    // the input row q becomes the level's pending row; row r moves up a level
+    const uint32_t oL = p.L[k];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        p.E[k][c] = iE[c]; p.X[k][c] = iX[c]; p.Y[k][c] = iY[c];
+        p.D[k][c] = dq[c]; p.G[k][c] = g0[c]; p.TX[k][c] = tXq[c];
+        iE[c] = oE[c]; iX[c] = oX[c]; iY[c] = oY[c];
+    }
+    p.L[k] = iL;
+    iL = oL;
+}
+
+template <int K>
+__global__ void __launch_bounds__(32) k_adj_blocked(const AdjBlockArgs b, const int64_t n_top) {
+    __shared__ float2 s_coef[256];
+    __shared__ float4 s_ring[2][K][32];
+    for (int i = threadIdx.x; i < b.a.n_coef; i += 32) s_coef[i] = b.a.coef[i];
+    __syncwarp();
+    if ((int)blockIdx.x >= b.n_tasks) return;
+    const AdjArgs& a = b.a;
+    constexpr int H = ((K + 3) / 4) * 4;
+    const int lane = threadIdx.x & 31;
+    const int strip = blockIdx.x % b.n_strips;
+    const int seg = blockIdx.x / b.n_strips;
+    AdjLane ln;
+    ln.y0 = b.seg_y0[seg];
+    ln.y1 = b.seg_y0[seg + 1];
+    ln.nx = a.nx; ln.ny = a.ny; ln.P = a.P;
+    const int xl = 4 * lane;
+    const int xg_pre = strip * b.w_int - H + xl;
+    ln.gx = ((xg_pre % ln.nx) + ln.nx) % ln.nx;
+    const bool col_ok = index_ok(ln.gx >= 0 && ln.gx + 4 <= ln.nx, kSiteRingColumn, a.dbg);
+    ln.own = (xl >= H) && (xl < H + b.w_int) && (xg_pre < ln.nx) && col_ok;
+    float4* ringE = &s_ring[0][0][lane];
+    float4* ringH = &s_ring[1][0][lane];
+    const float* tbs[K];                 // tape state of each level's step
+#pragma unroll
+    for (int k = 0; k < K; ++k) tbs[k] = b.tape[b.m_top - k];
+    AdjPipe<K> p;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            p.E[k][c] = 0.f; p.X[k][c] = 0.f; p.Y[k][c] = 0.f;
+            p.D[k][c] = 0.f; p.G[k][c] = 0.f; p.TX[k][c] = 0.f;
+        }
+        p.L[k] = 0u;
+    }
+    const size_t pitch = (size_t)a.pitch, lpitch = (size_t)a.lpitch;
+    const int ny = ln.ny, P = ln.P;
+    const int t_begin = (ln.y0 == 0) ? 0 : (ln.y0 - K);
+    const int t_end = ln.y1 + K;
+    const int lo = max(P, 1) + K;
+    const int sp[5] = {a.js, a.jr, a.jr + 1, a.jt, a.jt + 1};
+    auto is_lean = [&](int t) {
+        bool f = (t >= lo) && (t < ny - P);
+#pragma unroll
+        for (int s = 0; s < 5; ++s) f = f && ((unsigned)(t - sp[s]) > (unsigned)K);
+        return f;
+    };
+    // level-0 input rows, one row fetched ahead
+    float nE[4], nX[4], nY[4];
+    uint32_t nL = 0u;
+    auto fetch = [&](int row) {
+        if (row >= 0 && row < ny && col_ok) {
+            const size_t o = (size_t)row * pitch + ln.gx;
+            ld4g(b.lE_in + o, nE);
+            ld4g(b.lX_in + o, nX);
+            ld4g(b.lY_in + o, nY);
+            nL = __ldg(reinterpret_cast<const uint32_t*>(a.labels + (size_t)row * lpitch + ln.gx));
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) { nE[c] = 0.f; nX[c] = 0.f; nY[c] = 0.f; }
+            nL = 0u;
+        }
+    };
+    fetch(t_begin);
+#pragma unroll 1
+    for (int t = t_begin; t < t_end; ++t) {
+        float iE[4], iX[4], iY[4];
+        uint32_t iL = nL;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) { iE[c] = nE[c]; iX[c] = nX[c]; iY[c] = nY[c]; }
+        fetch(t + 1);
+        if (is_lean(t)) {
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                adj_level<K, false>(b, s_coef, p, k, t, n_top, tbs[k], iE, iX, iY, iL, ln, ringE,
+                                    ringH);
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                adj_level<K, true>(b, s_coef, p, k, t, n_top, tbs[k], iE, iX, iY, iL, ln, ringE,
+                                   ringH);
+        }
+        const int ro = t - K;
+        if (ln.own && ro >= ln.y0 && ro < ln.y1) {
+            const size_t o = (size_t)ro * pitch + ln.gx;
+            st4g(b.lE_out + o, iE);
+            st4g(b.lX_out + o, iX);
+            st4g(b.lY_out + o, iY);
+        }
+    }
+}
+
+bool launch_adj_blocked(const AdjBlockArgs& b, int K, int64_t n_top, cudaStream_t st) {
+    const unsigned grid = (unsigned)b.n_tasks;
+    switch (K) {
+        case 1: k_adj_blocked<1><<<grid, 32, 0, st>>>(b, n_top); return true;
+        case 2: k_adj_blocked<2><<<grid, 32, 0, st>>>(b, n_top); return true;
+        case 3: k_adj_blocked<3><<<grid, 32, 0, st>>>(b, n_top); return true;
+        case 4: k_adj_blocked<4><<<grid, 32, 0, st>>>(b, n_top); return true;
+        default: return false;
+    }
+}
+
 size_t state_floats(const fdtd_handle* h) {
     return (size_t)3 * h->pitch * h->g.ny + (size_t)2 * std::max(2 * h->g.pml_cells, 1) * h->pitch;
 }
@@ -661,9 +1004,10 @@ int fdtd_backward(fdtd_handle* h, double wR, double wT, double* g_eps, double* g
             ACK(cudaMemcpy(d_tape_ptrs, tape.data(), tape.size() * sizeof(float*),
                            cudaMemcpyHostToDevice));
         }
-        // lE[2] lX lY gA gB (f each) + mE[2] mH[2] (pr each)
-        ACK(cudaMalloc(&buf, (6 * f + 4 * pr) * sizeof(float)));
-        ACK(cudaMemsetAsync(buf, 0, (6 * f + 4 * pr) * sizeof(float), h->stream));
+        // lE[2] lX lY gA gB (f each) + mE[2] mH[2] (pr each) + the second lX, lY
+        // buffers of the blocked reverse kernel (f each)
+        ACK(cudaMalloc(&buf, (8 * f + 4 * pr) * sizeof(float)));
+        ACK(cudaMemsetAsync(buf, 0, (8 * f + 4 * pr) * sizeof(float), h->stream));
         ACK(cudaMalloc(&dbl, 2 * f * sizeof(double)));
         ACK(cudaMemsetAsync(dbl, 0, 2 * f * sizeof(double), h->stream));
         ACK(cudaMalloc(&dummy, (size_t)4 * nx * sizeof(double2)));
@@ -679,7 +1023,12 @@ int fdtd_backward(fdtd_handle* h, double wR, double wT, double* g_eps, double* g
         a.lX = buf + 2 * f; a.lY = buf + 3 * f; a.gA = buf + 4 * f; a.gB = buf + 5 * f;
         float* mEb[2] = {buf + 6 * f, buf + 6 * f + pr};
         float* mHb[2] = {buf + 6 * f + 2 * pr, buf + 6 * f + 3 * pr};
-        int pe_cur = 0, ph_cur = 0, le_cur = 0;
+        float* lXb[2] = {buf + 2 * f, buf + 6 * f + 4 * pr};
+        float* lYb[2] = {buf + 3 * f, buf + 7 * f + 4 * pr};
+        int pe_cur = 0, ph_cur = 0, le_cur = 0, lxy_cur = 0;
+        // reverse steps per launch: K-step blocked launches (labelled grids with
+        // nx % 4 == 0), else one launch pair per step
+        const int kb = (multi && h->opt_adj_block > 0) ? std::min(h->opt_adj_block, 4) : 0;
         double* GA = dbl;
         double* GB = dbl + f;
         const dim3 blk(256), grd((nx + 255) / 256, ny);
@@ -708,7 +1057,35 @@ int fdtd_backward(fdtd_handle* h, double wR, double wT, double* g_eps, double* g
                 for (int m = 0; m + 1 < L; ++m)
                     step_out_of_place(h, view(h, tape[m]), view(h, tape[m + 1]), c0 + m, dummy);
             }
-            for (int m = L - 1; m >= 0; --m) {
+            for (int m_top = L - 1; kb > 0 && m_top >= 0;) {
+                const int Kr = std::min(kb, m_top + 1);
+                const int keep = h->opt_seg;
+                h->opt_seg = 0;
+                BlockPlan& pl = get_plan(h, Kr);
+                h->opt_seg = keep;
+                AdjBlockArgs bb{};
+                bb.a = a;
+                bb.lE_in = lEb[le_cur]; bb.lE_out = lEb[le_cur ^ 1];
+                bb.lX_in = lXb[lxy_cur]; bb.lX_out = lXb[lxy_cur ^ 1];
+                bb.lY_in = lYb[lxy_cur]; bb.lY_out = lYb[lxy_cur ^ 1];
+                bb.mE_in = mEb[pe_cur]; bb.mE_out = mEb[pe_cur ^ 1];
+                bb.mH_in = mHb[ph_cur]; bb.mH_out = mHb[ph_cur ^ 1];
+                bb.tape = d_tape_ptrs;
+                bb.m_top = m_top;
+                bb.tape_f = f;
+                bb.seg_y0 = pl.d_seg_y0;
+                bb.n_strips = pl.n_strips;
+                bb.n_tasks = pl.n_strips * pl.n_segs;
+                bb.w_int = pl.w_int;
+                if (!launch_adj_blocked(bb, Kr, c0 + m_top, h->stream)) {
+                    h->err = "fdtd_backward: no blocked reverse kernel for this depth";
+                    throw Fail{FDTD_EINVAL};
+                }
+                le_cur ^= 1; lxy_cur ^= 1; pe_cur ^= 1; ph_cur ^= 1;
+                h->total_launches += 1;
+                m_top -= Kr;
+            }
+            for (int m = L - 1; kb == 0 && m >= 0; --m) {
                 const int64_t n = c0 + m;
                 const StateView v = view(h, tape[m]);
                 a.tE = v.E; a.tX = v.X; a.tY = v.Y; a.tPE = v.PE;
@@ -728,7 +1105,7 @@ int fdtd_backward(fdtd_handle* h, double wR, double wT, double* g_eps, double* g
                 le_cur ^= 1;
             }
             k_adj_flush<<<grd, blk, 0, h->stream>>>(a.gA, a.gB, GA, GB, nx, ny, pitch);
-            h->total_launches += 2 * L + 1;
+            h->total_launches += (kb ? 0 : 2 * L) + 1;
             ACK(cudaGetLastError());
         }
         // chain rule to (eps_r, sigma) per cell and (n, kappa) per label

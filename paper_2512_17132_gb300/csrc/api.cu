@@ -1249,6 +1249,10 @@ int fdtd_set_option(fdtd_handle* h, int32_t option, int64_t value) {
             if (value < 0) break;
             h->opt_watchdog = value;
             return FDTD_OK;
+        case FDTD_OPT_ADJ_BLOCK:
+            if (value < 0 || value > 4) break;
+            h->opt_adj_block = (int)value;
+            return FDTD_OK;
         case FDTD_OPT_DEBUG_TABLE_LIMIT:
 #ifdef FDTD_DEBUG_BOUNDS
             if (value < 0) break;

@@ -216,6 +216,7 @@ struct fdtd_handle {
     // options
     int opt_kernel = 0, opt_block = 8, opt_seg = 0, opt_timing = 0, opt_variant = 2;
     double opt_weight = 0.0;    // planner weight of a general-path iteration (0: default)
+    int opt_adj_block = 4;      // reverse steps per blocked adjoint launch (0: one per step)
     int64_t opt_watchdog = 0;
     // stats
     int64_t n = 0;

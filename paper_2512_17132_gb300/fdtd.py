@@ -20,6 +20,7 @@ FDTD_OPT_KERNEL, FDTD_OPT_BLOCK_STEPS, FDTD_OPT_SEG_ROWS = 1, 2, 3
 FDTD_OPT_TIMING, FDTD_OPT_WATCHDOG, FDTD_OPT_VARIANT, FDTD_OPT_GRAPH = 4, 5, 6, 7
 FDTD_OPT_PLAN_WEIGHT = 8
 FDTD_OPT_DEBUG_TABLE_LIMIT, FDTD_OPT_DEBUG_POKE_GUARD = 9, 10
+FDTD_OPT_ADJ_BLOCK = 11
 FDTD_POL_S, FDTD_POL_P = 0, 1
 KERNEL_AUTO, KERNEL_NAIVE, KERNEL_BLOCKED = 0, 1, 2
 

@@ -162,3 +162,28 @@ def test_label_gradients_match_finite_differences_full_config5(fd):
             fdv = (4.0 * fd_at(l, col, hh / 2) - fd_at(l, col, hh)) / 3.0
             print(f"label {l} {key}: adjoint {g[key][l]:.6e} fd {fdv:.6e}")
             assert abs(g[key][l] - fdv) <= 1e-3 * max(abs(fdv), 1e-2), (l, key)
+
+
+@pytest.mark.parametrize("spec_name", ["small", "crop", "c1b"])
+def test_blocked_reverse_steps_equal_per_step_kernels(fd, spec_name):
+    # K reverse steps per launch (FDTD_OPT_ADJ_BLOCK = 1..4) against one launch
+    # pair per step (0): the same expressions in the same order per cell, so
+    # the gradients agree bit for bit, for step counts that leave partial
+    # launches at the segment ends
+    if spec_name == "small":
+        spec, steps, every = _small(), 160, 37
+    elif spec_name == "crop":
+        spec, steps, every = _crop_c5(), 1500, 250
+    else:
+        spec, steps, every = config_c1b(steps=1600), 1600, 173
+    out = {}
+    for kb in (0, 1, 2, 3, 4):
+        with fd.Simulation(spec) as s:
+            fd.fdtd_set_option(s.h, fd.FDTD_OPT_ADJ_BLOCK, kb)
+            out[kb] = s.gradient(steps, 0.7, 0.3, every)
+    for kb in (1, 2, 3, 4):
+        for key in ("g_eps", "g_sigma"):
+            assert np.array_equal(out[kb][key], out[0][key]), (kb, key)
+        # the per-label sums are reduced with atomic FP64 adds (order not fixed)
+        for key in ("g_n", "g_k"):
+            np.testing.assert_allclose(out[kb][key], out[0][key], rtol=1e-12, atol=0)
