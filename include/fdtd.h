@@ -147,7 +147,7 @@ typedef struct fdtd_stats {
                                   kernel in lean iterations, times 1000 (0: the measured default,
                                   12 for S and 7.5 for P); batches take each handle's value */
 #define FDTD_OPT_ADJ_BLOCK 11    /* fdtd_backward: reverse steps per launch of the temporally
-                                  blocked reverse kernel, 1..4 (default 4), or 0 for one launch
+                                  blocked reverse kernel, 1..4 (default 3), or 0 for one launch
                                   pair per reverse step; labelled handles with nx % 4 == 0 (the
                                   others always take one step per launch); same gradients bit
                                   for bit */

@@ -528,6 +528,7 @@ __device__ __forceinline__ void st4g(float* p, const float (&v)[4]) {
 template <int K>
 struct AdjPipe {
     float E[K][4], X[K][4], Y[K][4], D[K][4], G[K][4], TX[K][4];
+    float GA[K][4], GB[K][4];           // running gradient sums of the pending row
     uint32_t L[K];
 };
 
@@ -544,29 +545,25 @@ struct AdjLane {
 template <int K, bool GENERAL>
 __device__ __forceinline__ void adj_level(const AdjBlockArgs& b, const float2* s_coef,
                                           AdjPipe<K>& p, const int k, const int t,
-                                          const int64_t n_top, const float* tb, float (&iE)[4],
-                                          float (&iX)[4], float (&iY)[4], uint32_t& iL,
-                                          const AdjLane& ln, float4* ringE, float4* ringH) {
+                                          const int64_t n_top, const float* tb,
+                                          const float4* tslot, float (&iE)[4], float (&iX)[4],
+                                          float (&iY)[4], float (&iA)[4], float (&iB)[4],
+                                          uint32_t& iL, const AdjLane& ln, float4* ringE,
+                                          float4* ringH) {
     const AdjArgs& a = b.a;
     const int q = t - k, r = q - 1;
     const int64_t n = n_top - k;
     const float S = a.S;
     const size_t pitch = (size_t)a.pitch;
     const bool r_ok = !GENERAL || (r >= 0 && r < ln.ny);
-    // taped forward state of step n: Ez, Hy of row r, Hx of row q
+    // taped forward state of step n (Ez, Hy of row r, Hx of row q), staged in
+    // shared memory one iteration ahead (zero outside the grid: Hx[ny] = 0)
     float tE[4], tY[4], tXq[4];
-    if (r_ok && index_ok(!GENERAL || (r >= 0 && r < ln.ny), kSiteTape, a.dbg)) {
-        ld4g(tb + (size_t)r * pitch + ln.gx, tE);
-        ld4g(tb + 2 * b.tape_f + (size_t)r * pitch + ln.gx, tY);
-    } else {
-#pragma unroll
-        for (int c = 0; c < 4; ++c) { tE[c] = 0.f; tY[c] = 0.f; }
-    }
-    if (!GENERAL || (q >= 0 && q < ln.ny)) {
-        ld4g(tb + b.tape_f + (size_t)q * pitch + ln.gx, tXq);
-    } else {
-#pragma unroll
-        for (int c = 0; c < 4; ++c) tXq[c] = 0.f;        // Hx[ny] = 0
+    {
+        const float4 e4 = tslot[0], y4 = tslot[32], x4 = tslot[64];
+        tE[0] = e4.x; tE[1] = e4.y; tE[2] = e4.z; tE[3] = e4.w;
+        tY[0] = y4.x; tY[1] = y4.y; tY[2] = y4.z; tY[3] = y4.w;
+        tXq[0] = x4.x; tXq[1] = x4.y; tXq[2] = x4.z; tXq[3] = x4.w;
     }
     // 1. transpose of the Hx update at edge q (adj_dez), psi_H carry of row q
     float dq[4];
@@ -610,7 +607,7 @@ __device__ __forceinline__ void adj_level(const AdjBlockArgs& b, const float2* s
             for (int c = 0; c < 4; ++c) dq[c] = __fmul_rn(S, x[c]);
         }
     }
-    float oE[4], oX[4], oY[4], g0[4];
+    float oE[4], oX[4], oY[4], g0[4], oA[4], oB[4];
     if (r_ok) {
         // 2. the adjoint of Ez^{n+1/2} after the H transposes (k_adj_h)
         const float yR = __shfl_down_sync(kFull, p.Y[k][0], 1);
@@ -642,19 +639,12 @@ __device__ __forceinline__ void adj_level(const AdjBlockArgs& b, const float2* s
                 curl[c] = __fadd_rn(dhy, dhx);
             }
         }
-        // 4. gradient sums of the owned cells (one lane per cell, level order = step order)
-        if (ln.own && r >= ln.y0 && r < ln.y1) {
-            const size_t o = (size_t)r * pitch + ln.gx;
-            float gA[4], gB[4];
-            ld4c(a.gA + o, gA);
-            ld4c(a.gB + o, gB);
+        // 4. gradient sums: they travel with the row from level to level (read
+        // by level 0, written after level K - 1), level order = step order
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                gA[c] = __fmaf_rn(eh[c], tE[c], gA[c]);
-                gB[c] = __fmaf_rn(eh[c], curl[c], gB[c]);
-            }
-            st4g(a.gA + o, gA);
-            st4g(a.gB + o, gB);
+        for (int c = 0; c < 4; ++c) {
+            oA[c] = __fmaf_rn(eh[c], tE[c], p.GA[k][c]);
+            oB[c] = __fmaf_rn(eh[c], curl[c], p.GB[k][c]);
         }
         // 5. transpose of the Ez update (adj_curl of row r), psi_E carry of row r
         const uint32_t L = p.L[k];
@@ -703,7 +693,9 @@ __device__ __forceinline__ void adj_level(const AdjBlockArgs& b, const float2* s
     } else {
         // outside the grid (warp-uniform): a zero row, which reaches no stored row
 #pragma unroll
-        for (int c = 0; c < 4; ++c) { oE[c] = 0.f; oX[c] = 0.f; oY[c] = 0.f; g0[c] = 0.f; }
+        for (int c = 0; c < 4; ++c) {
+            oE[c] = 0.f; oX[c] = 0.f; oY[c] = 0.f; g0[c] = 0.f; oA[c] = 0.f; oB[c] = 0.f;
+        }
     }
     // the input row q becomes the level's pending row; row r moves up a level
     const uint32_t oL = p.L[k];
@@ -711,16 +703,25 @@ __device__ __forceinline__ void adj_level(const AdjBlockArgs& b, const float2* s
     for (int c = 0; c < 4; ++c) {
         p.E[k][c] = iE[c]; p.X[k][c] = iX[c]; p.Y[k][c] = iY[c];
         p.D[k][c] = dq[c]; p.G[k][c] = g0[c]; p.TX[k][c] = tXq[c];
-        iE[c] = oE[c]; iX[c] = oX[c]; iY[c] = oY[c];
+        p.GA[k][c] = iA[c]; p.GB[k][c] = iB[c];
+        iE[c] = oE[c]; iX[c] = oX[c]; iY[c] = oY[c]; iA[c] = oA[c]; iB[c] = oB[c];
     }
     p.L[k] = iL;
     iL = oL;
+}
+
+__device__ __forceinline__ void cp16(void* smem, const void* gmem, int bytes) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(bytes)
+                 : "memory");
 }
 
 template <int K>
 __global__ void __launch_bounds__(32) k_adj_blocked(const AdjBlockArgs b, const int64_t n_top) {
     __shared__ float2 s_coef[256];
     __shared__ float4 s_ring[2][K][32];
+    // tape rows of each level, two iterations in flight: [slot][level][Ez, Hy, Hx][lane]
+    __shared__ float4 s_tape[2][K][3][32];
     for (int i = threadIdx.x; i < b.a.n_coef; i += 32) s_coef[i] = b.a.coef[i];
     __syncwarp();
     if ((int)blockIdx.x >= b.n_tasks) return;
@@ -750,6 +751,7 @@ __global__ void __launch_bounds__(32) k_adj_blocked(const AdjBlockArgs b, const 
         for (int c = 0; c < 4; ++c) {
             p.E[k][c] = 0.f; p.X[k][c] = 0.f; p.Y[k][c] = 0.f;
             p.D[k][c] = 0.f; p.G[k][c] = 0.f; p.TX[k][c] = 0.f;
+            p.GA[k][c] = 0.f; p.GB[k][c] = 0.f;
         }
         p.L[k] = 0u;
     }
@@ -765,8 +767,27 @@ __global__ void __launch_bounds__(32) k_adj_blocked(const AdjBlockArgs b, const 
         for (int s = 0; s < 5; ++s) f = f && ((unsigned)(t - sp[s]) > (unsigned)K);
         return f;
     };
-    // level-0 input rows, one row fetched ahead
-    float nE[4], nX[4], nY[4];
+    // tape rows needed at iteration t: level k reads Ez, Hy of row t - k - 1 and
+    // Hx of row t - k of its step; rows outside the grid are zero-filled
+    float4* tape_lane = &s_tape[0][0][0][lane];
+    auto stage_tape = [&](int t) {
+        const int slot = t & 1;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int r = t - k - 1, q = t - k;
+            const bool rok = r >= 0 && r < ny && col_ok, qok = q >= 0 && q < ny && col_ok;
+            const float* tb = tbs[k];
+            const size_t orow = (size_t)(rok ? r : 0) * pitch + ln.gx;
+            const size_t oq = (size_t)(qok ? q : 0) * pitch + ln.gx;
+            float4* dst = tape_lane + (slot * K + k) * 96;
+            cp16(dst, tb + orow, rok ? 16 : 0);
+            cp16(dst + 32, tb + 2 * b.tape_f + orow, rok ? 16 : 0);
+            cp16(dst + 64, tb + b.tape_f + oq, qok ? 16 : 0);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    // level-0 input rows (adjoint state and gradient sums), one row fetched ahead
+    float nE[4], nX[4], nY[4], nA[4], nB[4];
     uint32_t nL = 0u;
     auto fetch = [&](int row) {
         if (row >= 0 && row < ny && col_ok) {
@@ -774,31 +795,39 @@ __global__ void __launch_bounds__(32) k_adj_blocked(const AdjBlockArgs b, const 
             ld4g(b.lE_in + o, nE);
             ld4g(b.lX_in + o, nX);
             ld4g(b.lY_in + o, nY);
+            ld4c(a.gA + o, nA);
+            ld4c(a.gB + o, nB);
             nL = __ldg(reinterpret_cast<const uint32_t*>(a.labels + (size_t)row * lpitch + ln.gx));
         } else {
 #pragma unroll
-            for (int c = 0; c < 4; ++c) { nE[c] = 0.f; nX[c] = 0.f; nY[c] = 0.f; }
+            for (int c = 0; c < 4; ++c) { nE[c] = 0.f; nX[c] = 0.f; nY[c] = 0.f; nA[c] = 0.f; nB[c] = 0.f; }
             nL = 0u;
         }
     };
+    stage_tape(t_begin);
     fetch(t_begin);
 #pragma unroll 1
     for (int t = t_begin; t < t_end; ++t) {
-        float iE[4], iX[4], iY[4];
+        float iE[4], iX[4], iY[4], iA[4], iB[4];
         uint32_t iL = nL;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) { iE[c] = nE[c]; iX[c] = nX[c]; iY[c] = nY[c]; }
+        for (int c = 0; c < 4; ++c) {
+            iE[c] = nE[c]; iX[c] = nX[c]; iY[c] = nY[c]; iA[c] = nA[c]; iB[c] = nB[c];
+        }
+        stage_tape(t + 1);
         fetch(t + 1);
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");     // iteration t's rows
+        const float4* ts = tape_lane + (t & 1) * K * 96;
         if (is_lean(t)) {
 #pragma unroll
             for (int k = 0; k < K; ++k)
-                adj_level<K, false>(b, s_coef, p, k, t, n_top, tbs[k], iE, iX, iY, iL, ln, ringE,
-                                    ringH);
+                adj_level<K, false>(b, s_coef, p, k, t, n_top, tbs[k], ts + k * 96, iE, iX, iY, iA,
+                                    iB, iL, ln, ringE, ringH);
         } else {
 #pragma unroll
             for (int k = 0; k < K; ++k)
-                adj_level<K, true>(b, s_coef, p, k, t, n_top, tbs[k], iE, iX, iY, iL, ln, ringE,
-                                   ringH);
+                adj_level<K, true>(b, s_coef, p, k, t, n_top, tbs[k], ts + k * 96, iE, iX, iY, iA,
+                                   iB, iL, ln, ringE, ringH);
         }
         const int ro = t - K;
         if (ln.own && ro >= ln.y0 && ro < ln.y1) {
@@ -806,8 +835,11 @@ __global__ void __launch_bounds__(32) k_adj_blocked(const AdjBlockArgs b, const 
             st4g(b.lE_out + o, iE);
             st4g(b.lX_out + o, iX);
             st4g(b.lY_out + o, iY);
+            st4g(a.gA + o, iA);
+            st4g(a.gB + o, iB);
         }
     }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
 bool launch_adj_blocked(const AdjBlockArgs& b, int K, int64_t n_top, cudaStream_t st) {

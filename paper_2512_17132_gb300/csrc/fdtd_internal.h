@@ -121,10 +121,11 @@ void configure_twin_batch();
 void launch_twin_batch(const TwinArgs* tws, int n, int max_ny, int max_P,
                        const int64_t* step_base, int steps, cudaStream_t st);
 int blocked_max_K();
-// Code shape 5 (label-pair table, paired FP32): S polarisation, a label map
-// with at most 16 labels.
+// Code shape 5 (paired FP32; for S also the label-pair table): a label map
+// with at most 16 labels (P handles always have one).
 inline bool pair_shape_ok(bool pol_p, bool maps, int n_labels) {
-    return !pol_p && !maps && n_labels <= 16;
+    (void)pol_p;
+    return !maps && n_labels <= 16;
 }
 int blocked_warps_per_sm(int K, int variant, int pol = 0);
 
@@ -216,7 +217,7 @@ struct fdtd_handle {
     // options
     int opt_kernel = 0, opt_block = 8, opt_seg = 0, opt_timing = 0, opt_variant = 2;
     double opt_weight = 0.0;    // planner weight of a general-path iteration (0: default)
-    int opt_adj_block = 4;      // reverse steps per blocked adjoint launch (0: one per step)
+    int opt_adj_block = 3;      // reverse steps per blocked adjoint launch (0: one per step)
     int64_t opt_watchdog = 0;
     // stats
     int64_t n = 0;
