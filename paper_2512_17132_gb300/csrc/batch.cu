@@ -315,7 +315,7 @@ int batch_tune(fdtd_batch* b, int trials) {
     for (int K : {8, 7, 6}) {
         for (int v : {0, 1, 2, 3, 5}) {
             if (K == 8 && v == 1) continue;          // exceeds the register file at K = 8
-            if (b->hs[0]->src.polarization && v < 2) continue;   // P: shapes 2 and 3 only
+            if (b->hs[0]->src.polarization && v < 2) continue;   // P: shapes 2, 3 and 5
             if (v == 5 && !batch_pair_ok(b)) continue;
             const int s0 = model_seg(b, K, v);
             for (int f : {-1, 0, 1}) {

@@ -166,6 +166,58 @@ __device__ __forceinline__ void advance_lean_pair(Pipe<K>& p, float (&fE)[4], fl
     }
 }
 
+// Lean P iteration of code shape 5: the same pipeline as advance() for
+// POL = 1 with the loss-free centre update and the two edge differences
+// along s paired (f32x2); the centre's coefficient 1 is dropped (1 * F is F
+// exactly) and the lossy edge updates keep their per-edge label-pair
+// coefficients (scalar). Bit for bit the results of advance().
+template <int K>
+__device__ __forceinline__ void advance_lean_pair_p(Pipe<K>& p, float (&fE)[4], float (&fX)[4],
+                                                    float (&fY)[4], uint32_t& fL, const Lane& ln) {
+    const float2 S2 = f2(ln.S, ln.S);
+    const float2 M1 = f2(-1.0f, -1.0f);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const uint32_t cL = p.L[k];
+        const uint32_t lUp = p.L[k + 1];                          // row r-1
+        const uint32_t lNb = __shfl_up_sync(FULL, cL, 1) >> 24;   // column q-1 of lane 0
+        const uint32_t xP = (lUp << 4) | cL;
+        const uint32_t yP = (((cL << 8) | lNb) << 4) | cL;
+        const float yR = __shfl_down_sync(FULL, p.Y[k][0], 1);
+        const float2 dhx01 = __ffma2_rn(f2(p.X[k][0], p.X[k][1]), M1, f2(fX[0], fX[1]));
+        const float2 dhx23 = __ffma2_rn(f2(p.X[k][2], p.X[k][3]), M1, f2(fX[2], fX[3]));
+        const float2 dhy01 = f2(__fsub_rn(p.Y[k][1], p.Y[k][0]), __fsub_rn(p.Y[k][2], p.Y[k][1]));
+        const float2 dhy23 = f2(__fsub_rn(p.Y[k][3], p.Y[k][2]), __fsub_rn(yR, p.Y[k][3]));
+        const float2 e01 = __ffma2_rn(S2, __fadd2_rn(dhy01, dhx01), f2(p.E[k][0], p.E[k][1]));
+        const float2 e23 = __ffma2_rn(S2, __fadd2_rn(dhy23, dhx23), f2(p.E[k][2], p.E[k][3]));
+        const float2 d01 = __ffma2_rn(f2(p.E[k + 1][0], p.E[k + 1][1]), M1, e01);
+        const float2 d23 = __ffma2_rn(f2(p.E[k + 1][2], p.E[k + 1][3]), M1, e23);
+        const float oE[4] = {e01.x, e01.y, e23.x, e23.y};
+        const float d[4] = {d01.x, d01.y, d23.x, d23.y};
+        float oX[4], oY[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 cx = ln.coef[(xP >> (8 * q)) & 0xffu];
+            oX[q] = e_edge_new(cx.x, cx.y, p.X[k][q], d[q]);
+        }
+        const float eL = __shfl_up_sync(FULL, oE[3], 1);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float dy = __fsub_rn(oE[q], q > 0 ? oE[q - 1] : eL);
+            const float2 cy = ln.coef[(yP >> (8 * q)) & 0xffu];
+            oY[q] = e_edge_new(cy.x, cy.y, p.Y[k][q], dy);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            p.E[k][q] = fE[q]; p.X[k][q] = fX[q]; p.Y[k][q] = fY[q];
+            fE[q] = oE[q]; fX[q] = oX[q]; fY[q] = oY[q];
+        }
+        p.L[k] = fL;
+        fL = cL;
+        if (k == K - 1) p.L[K] = cL;
+    }
+}
+
 // One iteration of the pipeline: level k advances at row t-k-1, k = 0..K-1.
 // GENERAL = false is the lean path for iterations whose K rows hold no
 // CPML, source, monitor or boundary row and lie inside the valid range;
@@ -177,6 +229,10 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
                                         float4* ringH, const int64_t n0) {
     if constexpr (!GENERAL && kPairShape<V> && POL == 0) {
         advance_lean_pair<K>(p, fE, fX, fY, fL, ln);
+        return;
+    }
+    if constexpr (!GENERAL && kPairShape<V> && POL == 1) {
+        advance_lean_pair_p<K>(p, fE, fX, fY, fL, ln);
         return;
     }
     const float S = ln.S;
@@ -363,8 +419,10 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
 // under a register cap, see k_blocked_cap); 4 the ring, one row per trip,
 // that also stores the state after every intermediate step of the launch
 // (its owned rows) into BlockedArgs::tape, for the adjoint's recompute;
-// 5 (S polarisation, at most 16 labels) shape 2 with the label-pair table
-// and paired FP32 instructions on the lean path (advance_lean_pair).
+// 5 (at most 16 labels) shape 2 with paired FP32 instructions on the lean
+// path: for S with the label-pair coefficient table (advance_lean_pair),
+// for P on the centre update and the edge differences along s
+// (advance_lean_pair_p).
 template <int K, int V, int POL>
 __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float4* s_tab,
                                              const int task, const int64_t n0) {
@@ -467,7 +525,7 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float4*
                          (((fL >> 16) & 0xffu) < (unsigned)a.s.n_labels) &&
                          ((fL >> 24) < (unsigned)a.s.n_labels),
                      kSiteLabel, a.s.dbg);
-            if (kPairShape<V>) fL = pair_offsets(fL);
+            if (kPairShape<V> && POL == 0) fL = pair_offsets(fL);
             fE[0] = e4.x; fE[1] = e4.y; fE[2] = e4.z; fE[3] = e4.w;
             fX[0] = x4.x; fX[1] = x4.y; fX[2] = x4.z; fX[3] = x4.w;
             fY[0] = y4.x; fY[1] = y4.y; fY[2] = y4.z; fY[3] = y4.w;
@@ -550,7 +608,7 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float4*
 // built from the per-label table (labels < 16).
 template <int V, int POL>
 __device__ __forceinline__ void load_coef_table(const StepArgs& s, float4* s_tab) {
-    if (kPairShape<V>) {
+    if (kPairShape<V> && POL == 0) {
         const int last = s.n_labels - 1;
         for (int t = threadIdx.x; t < 256; t += 32) {
             const float2 c0 = s.coef[min(t & 15, last)], c1 = s.coef[min(t >> 4, last)];
@@ -566,7 +624,7 @@ __device__ __forceinline__ void load_coef_table(const StepArgs& s, float4* s_tab
 
 template <int K, int V, int POL>
 __device__ __forceinline__ void blocked_kernel_body(const BlockedArgs& a, const int64_t n0) {
-    __shared__ float4 s_tab[kPairShape<V> ? 256 : 128];
+    __shared__ float4 s_tab[(kPairShape<V> && POL == 0) ? 256 : 128];
     load_coef_table<V, POL>(a.s, s_tab);
     if ((int)blockIdx.x >= a.n_tasks) return;       // one warp per block and task
     blocked_task<K, V, POL>(a, s_tab, blockIdx.x, n0);
@@ -590,7 +648,7 @@ __global__ void __maxnreg__(224) k_blocked_cap(const BlockedArgs a,
 template <int K, int V, int POL>
 __device__ __forceinline__ void blocked_batch_body(const BatchArgs& b, const int step_off,
                                                    const int parity) {
-    __shared__ float4 s_tab[kPairShape<V> ? 256 : 128];
+    __shared__ float4 s_tab[(kPairShape<V> && POL == 0) ? 256 : 128];
     __shared__ __align__(16) unsigned char s_raw[sizeof(BlockedArgs)];
     const int task = blockIdx.x;
     if (task >= b.n_tasks) return;

@@ -54,7 +54,7 @@ def test_config1b_p_fields_and_rt(fd, ref_c1b_p, kernel, K):
     assert abs(R - rt[0]) < 1e-4 and abs(T - rt[1]) < 1e-4
 
 
-@pytest.mark.parametrize("variant", [2, 3])
+@pytest.mark.parametrize("variant", [2, 3, 5])
 @pytest.mark.parametrize("K,seg", [(8, None), (8, 27), (7, 41), (5, 19), (3, 22), (1, 18)])
 def test_p_blocked_is_bitwise_equal_to_naive(fd, K, seg, variant):
     spec = config_c1b(steps=411).with_(polarization=POL_P)
