@@ -474,7 +474,7 @@ def run_c4(args):
     b.build()
     from paper_2512_17132_gb300 import fdtd
     steps = args.fdtd_steps or 30000
-    specs = fi.config_c4(steps=steps)
+    specs = fi.config_c4(steps=steps, workers=os.cpu_count())
     cells = sum(sp.nx * sp.ny for sp in specs) * steps
     sims = [fdtd.Simulation(sp, timing=True) for sp in specs]
     batch = fdtd.Batch(sims, timing=True)

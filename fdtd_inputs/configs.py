@@ -226,31 +226,49 @@ def config_c3(lambda0: float = 550e-9, diseased: bool = False, seed: int = 0,
                  lambda0, rows, labels, leaf_materials(lambda0), **kw)
 
 
+def _c4_labels(job):
+    """Label map of one config-4 simulation (a top-level function, so that a
+    process pool can run it)."""
+    from .geometry import dicot_labels
+    nx, ny, dx, rows, seed, n_hyphae, coarse = job
+    return dicot_labels(nx, ny, dx, rows, seed=seed, n_hyphae=n_hyphae, coarse=coarse)
+
+
 def config_c4(n_sims: int = 64, seed: int = 0, steps: int = 30000,
-              nx: int = 2000, height_range=(2000, 12500), coarse: int = 4) -> list:
+              nx: int = 2000, height_range=(2000, 12500), coarse: int = 1,
+              workers: Optional[int] = None) -> list:
     """Config 4: independent dicot simulations of uneven height.
 
     Heights are uniform in height_range (rounded to 4 rows), wavelengths lie on
     a 400-2500 nm grid shuffled by the seed, even indices are healthy and odd
-    indices carry hyphae. Label maps are drawn `coarse` times coarser and
-    repeated (the layer edges are rounded to multiples of `coarse`).
+    indices carry hyphae. Label maps are drawn at the grid's own resolution
+    (coarse = 1); coarse > 1 draws them that many times coarser and repeats
+    each cell (the layer edges rounded to multiples of `coarse`). With
+    workers > 1 the maps are drawn in a process pool (spawned processes, safe
+    after CUDA has been initialised in the caller).
     """
-    from .geometry import dicot_labels
     rng = np.random.default_rng(seed)
     heights = (rng.integers(height_range[0], height_range[1] + 1, n_sims) // 4) * 4
     lams = 400e-9 + np.arange(n_sims) * (2100e-9 / max(1, n_sims - 1))
     lams = rng.permutation(lams)
-    specs = []
     dx = 20e-9
+    jobs, rows_all = [], []
     for i in range(n_sims):
         ny = int(heights[i])
         rows = dicot_rows(ny, dx)
-        rows["layer_edges"] = [e // coarse * coarse for e in rows["layer_edges"]]
-        labels = dicot_labels(nx, ny, dx, rows, seed=1000 + i,
-                              n_hyphae=(3 if i % 2 else 0), coarse=coarse)
-        specs.append(_base(f"c4-{i}", nx, ny, dx, steps, float(lams[i]), rows,
-                           labels, leaf_materials(float(lams[i]))))
-    return specs
+        if coarse > 1:
+            rows["layer_edges"] = [e // coarse * coarse for e in rows["layer_edges"]]
+        rows_all.append(rows)
+        jobs.append((nx, ny, dx, rows, 1000 + i, 3 if i % 2 else 0, coarse))
+    if workers and workers > 1:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            labels = list(ex.map(_c4_labels, jobs))
+    else:
+        labels = [_c4_labels(j) for j in jobs]
+    return [_base(f"c4-{i}", nx, int(heights[i]), dx, steps, float(lams[i]), rows_all[i],
+                  labels[i], leaf_materials(float(lams[i]))) for i in range(n_sims)]
 
 
 def config_c5(steps: int = 30000, nx: int = 1000, ny: int = 6000,

@@ -913,7 +913,7 @@ void step_out_of_place(fdtd_handle* h, const StateView& in, const StateView& out
 }
 
 // Recompute K steps n..n+K-1 from state `in` in one blocked launch (code
-// shape 4): the launch writes the final state to `out` and the states after
+// shape 6, or 4 for more than 16 labels): the launch writes the final state to `out` and the states after
 // the intermediate steps to tape_ptrs[0..K-2] (device array of state base
 // pointers); the same arithmetic as K one-step launches, so the same bits.
 void steps_to_tape(fdtd_handle* h, const StateView& in, const StateView& out, int K, int64_t n,
@@ -935,7 +935,9 @@ void steps_to_tape(fdtd_handle* h, const StateView& in, const StateView& out, in
     b.w_int = pl.w_int;
     b.tape = tape_ptrs;
     b.tape_f = (size_t)h->pitch * h->g.ny;
-    launch_blocked(b, K, 4, n, h->stream);
+    // code shape 6 (label-pair table, paired lean path) where the labels fit
+    const int shape = pair_shape_ok(false, h->maps, h->n_labels) ? 6 : 4;
+    launch_blocked(b, K, shape, n, h->stream);
 }
 
 }  // namespace

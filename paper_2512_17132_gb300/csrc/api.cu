@@ -1288,7 +1288,7 @@ int fdtd_set_option(fdtd_handle* h, int32_t option, int64_t value) {
             h->opt_weight = value / 1000.0;
             return FDTD_OK;
         case FDTD_OPT_VARIANT:
-            if (value < 0 || value > 5 || value == 4) break;
+            if (value < 0 || value > 5 || value == 4) break;   // 4 and 6: adjoint tape shapes
             if (value == 5 && !pair_shape_ok(h->src.polarization == FDTD_POL_P, h->maps,
                                              h->n_labels))
                 break;

@@ -108,7 +108,7 @@ __device__ __forceinline__ float4 pair_at(const float4* tab, uint32_t off) {
 // (ca, cb) of column q of a lane from its row's label word.
 // Code shapes that use the label-pair table (S polarisation).
 template <int V>
-constexpr bool kPairShape = (V == 5);
+constexpr bool kPairShape = (V == 5 || V == 6);
 
 template <int V>
 __device__ __forceinline__ float2 coef_s(const Lane& ln, uint32_t w, int q) {
@@ -127,9 +127,10 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 // intrinsic, and a - b is formed as fma(b, -1, a), which rounds like a
 // subtraction, so the results are bit for bit those of advance(). The
 // differences along x take a column pair shifted by one and stay scalar.
-template <int K>
+template <int K, int V>
 __device__ __forceinline__ void advance_lean_pair(Pipe<K>& p, float (&fE)[4], float (&fX)[4],
-                                                  float (&fY)[4], uint32_t& fL, const Lane& ln) {
+                                                  float (&fY)[4], uint32_t& fL, const Lane& ln,
+                                                  const BlockedArgs& a, const int t) {
     const float2 S2 = f2(ln.S, ln.S);
     const float2 M1 = f2(-1.0f, -1.0f);
 #pragma unroll
@@ -155,6 +156,17 @@ __device__ __forceinline__ void advance_lean_pair(Pipe<K>& p, float (&fE)[4], fl
         const float2 dy23 = f2(__fsub_rn(e23.x, e01.y), __fsub_rn(e23.y, e23.x));
         const float2 y01 = __ffma2_rn(S2, dy01, f2(p.Y[k][0], p.Y[k][1]));
         const float2 y23 = __ffma2_rn(S2, dy23, f2(p.Y[k][2], p.Y[k][3]));
+        if (V == 6 && k + 1 < K) {
+            // code shape 6: the state after step k+1 of this row (adjoint tape)
+            const int r = t - k - 1;
+            if (ln.own && r >= ln.y0 && r < ln.y1) {
+                float* tp = a.tape[k] + (size_t)r * a.s.pitch + ln.gx;
+                *reinterpret_cast<float4*>(tp) = make_float4(e01.x, e01.y, e23.x, e23.y);
+                *reinterpret_cast<float4*>(tp + a.tape_f) = make_float4(x01.x, x01.y, x23.x, x23.y);
+                *reinterpret_cast<float4*>(tp + 2 * a.tape_f) =
+                    make_float4(y01.x, y01.y, y23.x, y23.y);
+            }
+        }
         // level k now waits at row r+1; the new level-(k+1) row r flows up
 #pragma unroll
         for (int q = 0; q < 4; ++q) { p.E[k][q] = fE[q]; p.X[k][q] = fX[q]; p.Y[k][q] = fY[q]; }
@@ -228,7 +240,7 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
                                         const BlockedArgs& a, const Lane& ln, float4* ringE,
                                         float4* ringH, const int64_t n0) {
     if constexpr (!GENERAL && kPairShape<V> && POL == 0) {
-        advance_lean_pair<K>(p, fE, fX, fY, fL, ln);
+        advance_lean_pair<K, V>(p, fE, fX, fY, fL, ln, a, t);
         return;
     }
     if constexpr (!GENERAL && kPairShape<V> && POL == 1) {
@@ -287,7 +299,7 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
                         st4(a.psiE_out + (size_t)pe * a.s.pitch + ln.gx, psi);
                 } else {
                     ringE[(r % K) * 32] = make_float4(psi[0], psi[1], psi[2], psi[3]);
-                    if (V == 4 && ln.own && r >= ln.y0 && r < ln.y1)
+                    if ((V == 4 || V == 6) && ln.own && r >= ln.y0 && r < ln.y1)
                         st4(a.tape[k] + 3 * a.tape_f + (size_t)pe * a.s.pitch + ln.gx, psi);
                 }
             } else {
@@ -361,7 +373,7 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
                     oY[q] = h_new(p.Y[k][q], S, dy);
                 }
             }
-            if (V == 4 && k + 1 < K && ln.own && r >= ln.y0 && r < ln.y1 &&
+            if ((V == 4 || V == 6) && k + 1 < K && ln.own && r >= ln.y0 && r < ln.y1 &&
                 index_ok(r >= 0 && r < ln.ny && ln.col_ok, kSiteTape, a.s.dbg)) {
                 // code shape 4: the state after step k+1 of this row
                 float* t = a.tape[k] + (size_t)r * a.s.pitch + ln.gx;
@@ -422,7 +434,8 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
 // 5 (at most 16 labels) shape 2 with paired FP32 instructions on the lean
 // path: for S with the label-pair coefficient table (advance_lean_pair),
 // for P on the centre update and the edge differences along s
-// (advance_lean_pair_p).
+// (advance_lean_pair_p); 6 (S, at most 16 labels) shape 4 with the
+// label-pair table and the paired lean path (the adjoint's recompute).
 template <int K, int V, int POL>
 __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float4* s_tab,
                                              const int task, const int64_t n0) {

@@ -1,6 +1,6 @@
 // S-polarised (TMz) instances of the blocked kernel for single runs: code
-// shapes 0-5 at K = 1..8 (shape 4 serves the adjoint's recompute, shape 5
-// handles with at most 16 labels).
+// shapes 0-6 at K = 1..8 (shapes 4 and 6 serve the adjoint's recompute,
+// shapes 5 and 6 handles with at most 16 labels).
 #include "blocked_impl.cuh"
 
 namespace fdtd {
@@ -12,6 +12,7 @@ int blocked_occupancy_s(int K, int variant) {
         if (variant == 3) return occupancy_of(k_blocked_cap<k, 0>);            \
         if (variant == 4) return occupancy_of(k_blocked<k, 4, 0>);             \
         if (variant == 5) return occupancy_of(k_blocked<k, 5, 0>);             \
+        if (variant == 6) return occupancy_of(k_blocked<k, 6, 0>);             \
         if (variant == 2) return occupancy_of(k_blocked<k, 2, 0>);             \
         return variant ? occupancy_of(k_blocked<k, 1, 0>) : occupancy_of(k_blocked<k, 0, 0>);
         FDTD_BLOCKED_CASES(X)
@@ -28,6 +29,7 @@ bool launch_blocked_s(const BlockedArgs& a, int K, int variant, int64_t n0, cuda
         if (variant == 3) k_blocked_cap<k, 0><<<grid, 32, 0, st>>>(a, n0);     \
         else if (variant == 4) k_blocked<k, 4, 0><<<grid, 32, 0, st>>>(a, n0); \
         else if (variant == 5) k_blocked<k, 5, 0><<<grid, 32, 0, st>>>(a, n0); \
+        else if (variant == 6) k_blocked<k, 6, 0><<<grid, 32, 0, st>>>(a, n0); \
         else if (variant == 2) k_blocked<k, 2, 0><<<grid, 32, 0, st>>>(a, n0); \
         else if (variant) k_blocked<k, 1, 0><<<grid, 32, 0, st>>>(a, n0);      \
         else k_blocked<k, 0, 0><<<grid, 32, 0, st>>>(a, n0);                   \

@@ -187,3 +187,22 @@ def test_blocked_reverse_steps_equal_per_step_kernels(fd, spec_name):
         # the per-label sums are reduced with atomic FP64 adds (order not fixed)
         for key in ("g_n", "g_k"):
             np.testing.assert_allclose(out[kb][key], out[0][key], rtol=1e-12, atol=0)
+
+
+def test_pair_recompute_equals_scalar_recompute(fd):
+    # with <= 16 labels the forward runs code shape 5 and the adjoint's
+    # recompute shape 6 (label-pair table, paired FP32); padding the material
+    # table past 16 labels (the extra labels unused) forces shapes 2 and 4.
+    # Both round identically, so the gradients agree bit for bit.
+    spec = _crop_c5().with_(steps=1500)
+    pad = np.vstack([spec.materials, np.tile([[1.3, 0.0]], (14, 1))])
+    out = []
+    for sp in (spec, spec.with_(materials=pad)):
+        with fd.Simulation(sp) as s:
+            g = s.gradient(1500, 1.0, 0.5, 250)
+            out.append((g, s.stats()["variant"]))
+    (ga, va), (gb, vb) = out
+    assert va == 5 and vb == 2
+    for key in ("g_eps", "g_sigma"):
+        assert np.array_equal(ga[key], gb[key]), key
+    np.testing.assert_allclose(gb["g_n"][:len(spec.materials)], ga["g_n"], rtol=1e-12, atol=0)
