@@ -722,6 +722,9 @@ __global__ void __launch_bounds__(32) k_adj_blocked(const AdjBlockArgs b, const 
     __shared__ float4 s_ring[2][K][32];
     // tape rows of each level, two iterations in flight: [slot][level][Ez, Hy, Hx][lane]
     __shared__ float4 s_tape[2][K][3][32];
+    // level-0 input row (lE, lX, lY, gA, gB) and its labels, same two slots
+    __shared__ float4 s_in[2][5][32];
+    __shared__ uint32_t s_lab[2][32];
     for (int i = threadIdx.x; i < b.a.n_coef; i += 32) s_coef[i] = b.a.coef[i];
     __syncwarp();
     if ((int)blockIdx.x >= b.n_tasks) return;
@@ -786,37 +789,42 @@ __global__ void __launch_bounds__(32) k_adj_blocked(const AdjBlockArgs b, const 
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
-    // level-0 input rows (adjoint state and gradient sums), one row fetched ahead
-    float nE[4], nX[4], nY[4], nA[4], nB[4];
-    uint32_t nL = 0u;
-    auto fetch = [&](int row) {
-        if (row >= 0 && row < ny && col_ok) {
-            const size_t o = (size_t)row * pitch + ln.gx;
-            ld4g(b.lE_in + o, nE);
-            ld4g(b.lX_in + o, nX);
-            ld4g(b.lY_in + o, nY);
-            ld4c(a.gA + o, nA);
-            ld4c(a.gB + o, nB);
-            nL = __ldg(reinterpret_cast<const uint32_t*>(a.labels + (size_t)row * lpitch + ln.gx));
-        } else {
-#pragma unroll
-            for (int c = 0; c < 4; ++c) { nE[c] = 0.f; nX[c] = 0.f; nY[c] = 0.f; nA[c] = 0.f; nB[c] = 0.f; }
-            nL = 0u;
-        }
+    // level-0 input rows (adjoint state and gradient sums) and labels, staged
+    // with the tape rows of the same iteration (zero outside the grid)
+    auto stage_in = [&](int row) {
+        const int slot = row & 1;
+        const bool ok = row >= 0 && row < ny && col_ok;
+        const size_t o = (size_t)(ok ? row : 0) * pitch + ln.gx;
+        const int nb = ok ? 16 : 0;
+        float4* d = &s_in[0][0][lane] + slot * 160;
+        cp16(d, b.lE_in + o, nb);
+        cp16(d + 32, b.lX_in + o, nb);
+        cp16(d + 64, b.lY_in + o, nb);
+        cp16(d + 96, a.gA + o, nb);
+        cp16(d + 128, a.gB + o, nb);
+        const unsigned sa = (unsigned)__cvta_generic_to_shared(&s_lab[slot][lane]);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa),
+                     "l"(a.labels + (size_t)(ok ? row : 0) * lpitch + ln.gx), "r"(ok ? 4 : 0)
+                     : "memory");
     };
-    stage_tape(t_begin);
-    fetch(t_begin);
+    stage_in(t_begin);
+    stage_tape(t_begin);                 // commits the group of iteration t_begin
 #pragma unroll 1
     for (int t = t_begin; t < t_end; ++t) {
-        float iE[4], iX[4], iY[4], iA[4], iB[4];
-        uint32_t iL = nL;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            iE[c] = nE[c]; iX[c] = nX[c]; iY[c] = nY[c]; iA[c] = nA[c]; iB[c] = nB[c];
-        }
+        stage_in(t + 1);
         stage_tape(t + 1);
-        fetch(t + 1);
         asm volatile("cp.async.wait_group 1;\n" ::: "memory");     // iteration t's rows
+        float iE[4], iX[4], iY[4], iA[4], iB[4];
+        {
+            const float4* src = &s_in[0][0][lane] + (t & 1) * 160;
+            float* dst[5] = {iE, iX, iY, iA, iB};
+#pragma unroll
+            for (int f = 0; f < 5; ++f) {
+                const float4 v = src[32 * f];
+                dst[f][0] = v.x; dst[f][1] = v.y; dst[f][2] = v.z; dst[f][3] = v.w;
+            }
+        }
+        uint32_t iL = s_lab[t & 1][lane];
         const float4* ts = tape_lane + (t & 1) * K * 96;
         if (is_lean(t)) {
 #pragma unroll
@@ -840,6 +848,52 @@ __global__ void __launch_bounds__(32) k_adj_blocked(const AdjBlockArgs b, const 
         }
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+int adj_blocked_per_sm(int K) {
+    int v = 0;
+    cudaError_t e = cudaSuccess;
+    switch (K) {
+        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_adj_blocked<1>, 32, 0); break;
+        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_adj_blocked<2>, 32, 0); break;
+        case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_adj_blocked<3>, 32, 0); break;
+        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_adj_blocked<4>, 32, 0); break;
+        default: return 0;
+    }
+    return e == cudaSuccess ? v : 0;
+}
+
+// Segment plan of the blocked reverse kernel for depth K: the forward
+// planner's cuts (segment_bounds) for the segment count that minimises
+// waves x (rows + 2K) with this kernel's own occupancy.
+struct AdjPlan {
+    int K = 0, n_strips = 0, n_segs = 0, w_int = 0;
+    int* d_seg = nullptr;
+};
+
+AdjPlan make_adj_plan(fdtd_handle* h, int K) {
+    AdjPlan pl;
+    pl.K = K;
+    const int halo = (K + 3) / 4 * 4;
+    pl.w_int = 128 - 2 * halo;
+    pl.n_strips = (h->g.nx + pl.w_int - 1) / pl.w_int;
+    int per_sm = adj_blocked_per_sm(K);
+    if (per_sm <= 0) per_sm = 8;
+    const int64_t W = (int64_t)sm_count(h) * per_sm;
+    const int ny = h->g.ny;
+    double best = 1e300;
+    int seg = ny;
+    for (int n = 1; n <= std::max(1, ny / (K + 1)); ++n) {
+        const int64_t waves = ((int64_t)n * pl.n_strips + W - 1) / W;
+        const double rows = std::ceil((double)ny / n);
+        const double cost = (double)waves * (rows + 2.0 * K);
+        if (cost < best - 1e-9) { best = cost; seg = (int)rows; }
+    }
+    const std::vector<int> bnd = segment_bounds(h->g, std::max(seg, K + 1), K, 0, h->opt_weight);
+    pl.n_segs = (int)bnd.size() - 1;
+    ACK(cudaMalloc(&pl.d_seg, bnd.size() * sizeof(int)));
+    ACK(cudaMemcpy(pl.d_seg, bnd.data(), bnd.size() * sizeof(int), cudaMemcpyHostToDevice));
+    return pl;
 }
 
 bool launch_adj_blocked(const AdjBlockArgs& b, int K, int64_t n_top, cudaStream_t st) {
@@ -986,11 +1040,13 @@ int fdtd_backward(fdtd_handle* h, double wR, double wT, double* g_eps, double* g
                   double* g_label, double out[3]) {
     if (!h) return FDTD_EINVAL;
     std::vector<float*> tape;
+    std::vector<AdjPlan> adj_plans;
     float* buf = nullptr;
     double* dbl = nullptr;
     double2* dummy = nullptr;
     float** d_tape_ptrs = nullptr;
     auto cleanup = [&]() {
+        for (auto& pl : adj_plans) if (pl.d_seg) cudaFree(pl.d_seg);
         if (d_tape_ptrs) cudaFree(d_tape_ptrs);
         for (auto& t : tape) cudaFree(t);
         if (buf) cudaFree(buf);
@@ -1093,10 +1149,14 @@ int fdtd_backward(fdtd_handle* h, double wR, double wT, double* g_eps, double* g
             }
             for (int m_top = L - 1; kb > 0 && m_top >= 0;) {
                 const int Kr = std::min(kb, m_top + 1);
-                const int keep = h->opt_seg;
-                h->opt_seg = 0;
-                BlockPlan& pl = get_plan(h, Kr);
-                h->opt_seg = keep;
+                AdjPlan* plp = nullptr;
+                for (auto& q : adj_plans)
+                    if (q.K == Kr) plp = &q;
+                if (!plp) {
+                    adj_plans.push_back(make_adj_plan(h, Kr));
+                    plp = &adj_plans.back();
+                }
+                const AdjPlan& pl = *plp;
                 AdjBlockArgs bb{};
                 bb.a = a;
                 bb.lE_in = lEb[le_cur]; bb.lE_out = lEb[le_cur ^ 1];
@@ -1107,7 +1167,7 @@ int fdtd_backward(fdtd_handle* h, double wR, double wT, double* g_eps, double* g
                 bb.tape = d_tape_ptrs;
                 bb.m_top = m_top;
                 bb.tape_f = f;
-                bb.seg_y0 = pl.d_seg_y0;
+                bb.seg_y0 = pl.d_seg;
                 bb.n_strips = pl.n_strips;
                 bb.n_tasks = pl.n_strips * pl.n_segs;
                 bb.w_int = pl.w_int;
