@@ -710,6 +710,8 @@ __device__ __forceinline__ void adj_level(const AdjBlockArgs& b, const float2* s
     iL = oL;
 }
 
+constexpr int kAdjRing = 2;   // ring slots of the blocked reverse kernel's staged rows (3 measured slower)
+
 __device__ __forceinline__ void cp16(void* smem, const void* gmem, int bytes) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(bytes)
@@ -720,11 +722,12 @@ template <int K>
 __global__ void __launch_bounds__(32) k_adj_blocked(const AdjBlockArgs b, const int64_t n_top) {
     __shared__ float2 s_coef[256];
     __shared__ float4 s_ring[2][K][32];
-    // tape rows of each level, two iterations in flight: [slot][level][Ez, Hy, Hx][lane]
-    __shared__ float4 s_tape[2][K][3][32];
-    // level-0 input row (lE, lX, lY, gA, gB) and its labels, same two slots
-    __shared__ float4 s_in[2][5][32];
-    __shared__ uint32_t s_lab[2][32];
+    // tape rows of each level, kAdjRing iterations in flight:
+    // [slot][level][Ez, Hy, Hx][lane]
+    __shared__ float4 s_tape[kAdjRing][K][3][32];
+    // level-0 input row (lE, lX, lY, gA, gB) and its labels, same slots
+    __shared__ float4 s_in[kAdjRing][5][32];
+    __shared__ uint32_t s_lab[kAdjRing][32];
     for (int i = threadIdx.x; i < b.a.n_coef; i += 32) s_coef[i] = b.a.coef[i];
     __syncwarp();
     if ((int)blockIdx.x >= b.n_tasks) return;
@@ -774,7 +777,7 @@ __global__ void __launch_bounds__(32) k_adj_blocked(const AdjBlockArgs b, const 
     // Hx of row t - k of its step; rows outside the grid are zero-filled
     float4* tape_lane = &s_tape[0][0][0][lane];
     auto stage_tape = [&](int t) {
-        const int slot = t & 1;
+        const int slot = t % kAdjRing;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int r = t - k - 1, q = t - k;
@@ -792,7 +795,7 @@ __global__ void __launch_bounds__(32) k_adj_blocked(const AdjBlockArgs b, const 
     // level-0 input rows (adjoint state and gradient sums) and labels, staged
     // with the tape rows of the same iteration (zero outside the grid)
     auto stage_in = [&](int row) {
-        const int slot = row & 1;
+        const int slot = row % kAdjRing;
         const bool ok = row >= 0 && row < ny && col_ok;
         const size_t o = (size_t)(ok ? row : 0) * pitch + ln.gx;
         const int nb = ok ? 16 : 0;
@@ -807,16 +810,20 @@ __global__ void __launch_bounds__(32) k_adj_blocked(const AdjBlockArgs b, const 
                      "l"(a.labels + (size_t)(ok ? row : 0) * lpitch + ln.gx), "r"(ok ? 4 : 0)
                      : "memory");
     };
-    stage_in(t_begin);
-    stage_tape(t_begin);                 // commits the group of iteration t_begin
+    // one commit group per iteration, kAdjRing - 1 iterations ahead
+#pragma unroll
+    for (int d = 0; d < kAdjRing - 1; ++d) {
+        stage_in(t_begin + d);
+        stage_tape(t_begin + d);
+    }
 #pragma unroll 1
     for (int t = t_begin; t < t_end; ++t) {
-        stage_in(t + 1);
-        stage_tape(t + 1);
-        asm volatile("cp.async.wait_group 1;\n" ::: "memory");     // iteration t's rows
+        stage_in(t + kAdjRing - 1);
+        stage_tape(t + kAdjRing - 1);
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(kAdjRing - 1) : "memory");  // iteration t
         float iE[4], iX[4], iY[4], iA[4], iB[4];
         {
-            const float4* src = &s_in[0][0][lane] + (t & 1) * 160;
+            const float4* src = &s_in[0][0][lane] + (t % kAdjRing) * 160;
             float* dst[5] = {iE, iX, iY, iA, iB};
 #pragma unroll
             for (int f = 0; f < 5; ++f) {
@@ -824,8 +831,8 @@ __global__ void __launch_bounds__(32) k_adj_blocked(const AdjBlockArgs b, const 
                 dst[f][0] = v.x; dst[f][1] = v.y; dst[f][2] = v.z; dst[f][3] = v.w;
             }
         }
-        uint32_t iL = s_lab[t & 1][lane];
-        const float4* ts = tape_lane + (t & 1) * K * 96;
+        uint32_t iL = s_lab[t % kAdjRing][lane];
+        const float4* ts = tape_lane + (t % kAdjRing) * K * 96;
         if (is_lean(t)) {
 #pragma unroll
             for (int k = 0; k < K; ++k)
