@@ -11,6 +11,11 @@ and bench.py compare the CUDA library with these files.
       config 3 (healthy monocot, 550 nm, dx = 15 nm) cropped to its first
       8192 rows (the whole leaf and both monitors) and 2048 columns, with R, T
       and the DFT lines after 4000 and after 60 000 steps.
+  python tests/golden/make_oracle_goldens.py c5fd [--threads N]
+      config 5 (the config-1 stack at 1000 x 6000, 550 nm) over 6000 steps:
+      R and its central differences (h = 1e-4) with respect to eps_r at 32
+      random cells of the stack region (rows 30-259, seed 7) and to n and
+      kappa of every label, all in FP64.
   python tests/golden/make_oracle_goldens.py e2 [--threads N]
       the validation cylinder array of Sec. 3 (100 x 897 cells, h = 0.01 m),
       60 000 steps, S and P polarisation, at L/lambda = 0.75, 0.82, 0.855
@@ -35,7 +40,8 @@ ROOT = os.path.dirname(os.path.dirname(HERE))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-from fdtd_inputs import config_c2, config_c3, config_e2, crop_layout  # noqa: E402
+from fdtd_inputs import config_c2, config_c3, config_c5, config_e2, crop_layout  # noqa: E402
+from oracle import eps_sigma  # noqa: E402
 from oracle.fdtd_tez import TEzOracle, empty_twin_tez  # noqa: E402
 from oracle.fdtd_tmz import empty_twin  # noqa: E402
 from oracle.fdtd_tmz_c import TMzOracleC  # noqa: E402
@@ -129,6 +135,59 @@ def run_e2(threads):
                     dict(l_over_lambda=x))
 
 
+def c5fd_cells(ny, nx):
+    """The 32 cells of the config-5 finite differences: rows 30-259 (the
+    stack between the monitors), any column, numpy default_rng(7)."""
+    rng = np.random.default_rng(7)
+    return np.stack([rng.integers(30, 260, 32), rng.integers(0, nx, 32)], axis=1)
+
+
+def run_c5fd(threads, steps=6000, h=1e-4, spec=None, out_name="c5fd"):
+    spec = config_c5(steps=steps) if spec is None else spec
+    t0 = time.time()
+    twin = empty_twin(spec).run(steps)
+    p_inc = twin.fluxes()[1] * spec.nx
+    omega = 2.0 * np.pi * 299_792_458.0 / spec.lambda0
+    mats = np.asarray(spec.materials, dtype=np.float64)
+
+    def reflectance(eps, sig):
+        leaf = TMzOracleC(spec, eps_r=eps, sigma=sig).run(steps, threads)
+        return leaf.fluxes()[0] / p_inc
+
+    def maps(m):
+        return eps_sigma(m[spec.labels, 0], m[spec.labels, 1], omega)
+
+    eps0, sig0 = maps(mats)
+    R0 = reflectance(eps0, sig0)
+    cells = c5fd_cells(spec.ny, spec.nx)
+    g_eps = []
+    for j, i in cells:
+        e = eps0.copy()
+        e[j, i] += h
+        rp = reflectance(e, sig0)
+        e[j, i] -= 2.0 * h
+        rm = reflectance(e, sig0)
+        g_eps.append((rp - rm) / (2.0 * h))
+        print(f"cell ({j}, {i}): dR/deps = {g_eps[-1]:.9e}", flush=True)
+    g_n, g_k = [], []
+    for lab in range(len(mats)):
+        for col, out in ((0, g_n), (1, g_k)):
+            m = mats.copy()
+            m[lab, col] += h
+            rp = reflectance(*maps(m))
+            m[lab, col] -= 2.0 * h
+            rm = reflectance(*maps(m))
+            out.append((rp - rm) / (2.0 * h))
+    rec = dict(case=out_name, nx=spec.nx, ny=spec.ny, steps=int(steps), lambda0=spec.lambda0,
+               h=h, R=R0, cells=cells.tolist(), g_eps=g_eps, g_n=g_n, g_k=g_k,
+               oracle="FP64 oracle (TMzOracle state, C time loop TMzOracleC), central differences",
+               threads=int(threads), wall_s=round(time.time() - t0, 1),
+               command=f"python tests/golden/make_oracle_goldens.py c5fd --threads {threads}")
+    with open(os.path.join(HERE, f"oracle_{out_name}.json"), "w") as f:
+        json.dump(rec, f, indent=1)
+    print(json.dumps({k: rec[k] for k in ("case", "steps", "R", "wall_s")}), flush=True)
+
+
 def main(argv):
     threads = os.cpu_count() or 1
     if "--threads" in argv:
@@ -143,6 +202,8 @@ def main(argv):
         run_c3crop(threads)
     elif case == "e2":
         run_e2(threads)
+    elif case == "c5fd":
+        run_c5fd(threads)
     else:
         raise SystemExit(__doc__)
 

@@ -206,3 +206,45 @@ def test_pair_recompute_equals_scalar_recompute(fd):
     for key in ("g_eps", "g_sigma"):
         assert np.array_equal(ga[key], gb[key]), key
     np.testing.assert_allclose(gb["g_n"][:len(spec.materials)], ga["g_n"], rtol=1e-12, atol=0)
+
+
+def _c5fd():
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_c5fd.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        return json.load(f)
+
+
+C5FD = _c5fd()
+
+
+@pytest.mark.skipif(C5FD is None, reason="no config-5 finite-difference golden written")
+def test_full_size_config5_gradient_matches_fp64_finite_differences(fd):
+    # config 5 at full size (1000 x 6000, the config-1 stack), R(550 nm) over
+    # the stored step count: the FP32 adjoint against FP64 central
+    # differences (h = 1e-4) of the oracle at 32 random cells of the stack
+    # and for n, kappa of every label. Bound: 1e-3 relative, the vector norm
+    # for the cells plus a per-cell check with a floor of 1e-3 of the largest
+    # entry (cells with a near-zero derivative), per label 1e-3 of the
+    # largest label derivative.
+    g = C5FD
+    spec = config_c5(steps=g["steps"])
+    assert (spec.nx, spec.ny) == (g["nx"], g["ny"])
+    with fd.Simulation(spec) as s:
+        got = s.gradient(g["steps"], 1.0, 0.0, 500)
+    assert abs(got["R"] - g["R"]) < 1e-5
+    cells = np.asarray(g["cells"])
+    ge = got["g_eps"][cells[:, 0], cells[:, 1]]
+    ref = np.asarray(g["g_eps"])
+    rel = np.linalg.norm(ge - ref) / np.linalg.norm(ref)
+    worst = np.abs(ge - ref).max() / np.abs(ref).max()
+    print(f"32 cells: relative L2 {rel:.2e}, worst entry {worst:.2e} of the largest; "
+          f"labels n {np.asarray(got['g_n'])} vs {np.asarray(g['g_n'])}, "
+          f"kappa {np.asarray(got['g_k'])} vs {np.asarray(g['g_k'])}")
+    assert rel <= TOL and worst <= TOL
+    for key in ("g_n", "g_k"):
+        r = np.asarray(g[key])
+        assert np.abs(np.asarray(got[key]) - r).max() <= TOL * np.abs(r).max(), key
