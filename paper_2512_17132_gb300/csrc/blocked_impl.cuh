@@ -82,6 +82,7 @@ template <int K>
 struct Pipe {
     float E[K + 1][4], X[K + 1][4], Y[K][4];
     uint32_t L[K + 1];
+    uint32_t LY[K];   // P, code shape 5: left-edge label pairs of the pending row
 };
 
 struct Lane {
@@ -185,16 +186,14 @@ __device__ __forceinline__ void advance_lean_pair(Pipe<K>& p, float (&fE)[4], fl
 // coefficients (scalar). Bit for bit the results of advance().
 template <int K>
 __device__ __forceinline__ void advance_lean_pair_p(Pipe<K>& p, float (&fE)[4], float (&fX)[4],
-                                                    float (&fY)[4], uint32_t& fL, const Lane& ln) {
+                                                    float (&fY)[4], uint32_t& fL, uint32_t& fLY,
+                                                    const Lane& ln) {
     const float2 S2 = f2(ln.S, ln.S);
     const float2 M1 = f2(-1.0f, -1.0f);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        const uint32_t cL = p.L[k];
-        const uint32_t lUp = p.L[k + 1];                          // row r-1
-        const uint32_t lNb = __shfl_up_sync(FULL, cL, 1) >> 24;   // column q-1 of lane 0
-        const uint32_t xP = (lUp << 4) | cL;
-        const uint32_t yP = (((cL << 8) | lNb) << 4) | cL;
+        // the row's edge label pairs, formed once when the row was loaded
+        const uint32_t xP = p.L[k], yP = p.LY[k];
         const float yR = __shfl_down_sync(FULL, p.Y[k][0], 1);
         const float2 dhx01 = __ffma2_rn(f2(p.X[k][0], p.X[k][1]), M1, f2(fX[0], fX[1]));
         const float2 dhx23 = __ffma2_rn(f2(p.X[k][2], p.X[k][3]), M1, f2(fX[2], fX[3]));
@@ -225,8 +224,9 @@ __device__ __forceinline__ void advance_lean_pair_p(Pipe<K>& p, float (&fE)[4], 
             fE[q] = oE[q]; fX[q] = oX[q]; fY[q] = oY[q];
         }
         p.L[k] = fL;
-        fL = cL;
-        if (k == K - 1) p.L[K] = cL;
+        fL = xP;
+        p.LY[k] = fLY;
+        fLY = yP;
     }
 }
 
@@ -236,7 +236,7 @@ __device__ __forceinline__ void advance_lean_pair_p(Pipe<K>& p, float (&fE)[4], 
 // both paths round identically.
 template <int K, bool GENERAL, int POL, int V>
 __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[4],
-                                        float (&fY)[4], uint32_t& fL, const int t,
+                                        float (&fY)[4], uint32_t& fL, uint32_t& fLY, const int t,
                                         const BlockedArgs& a, const Lane& ln, float4* ringE,
                                         float4* ringH, const int64_t n0) {
     if constexpr (!GENERAL && kPairShape<V> && POL == 0) {
@@ -244,7 +244,7 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
         return;
     }
     if constexpr (!GENERAL && kPairShape<V> && POL == 1) {
-        advance_lean_pair_p<K>(p, fE, fX, fY, fL, ln);
+        advance_lean_pair_p<K>(p, fE, fX, fY, fL, fLY, ln);
         return;
     }
     const float S = ln.S;
@@ -255,7 +255,10 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
         const uint32_t cL = p.L[k];
         // P: packed label-pair indices (labels < 16) of the top and left edges
         uint32_t xP = 0u, yP = 0u;
-        if (POL == 1) {
+        if (POL == 1 && kPairShape<V>) {
+            xP = cL;                        // formed when the row was loaded
+            yP = p.LY[k];
+        } else if (POL == 1) {
             const uint32_t lUp = p.L[k + 1];                          // row r-1
             const uint32_t lNb = __shfl_up_sync(FULL, cL, 1) >> 24;   // column q-1 of lane 0
             xP = (lUp << 4) | cL;
@@ -419,6 +422,11 @@ __device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[
         }
         p.L[k] = fL;
         fL = cL;
+        if (POL == 1 && kPairShape<V>) {
+            const uint32_t cY = p.LY[k];
+            p.LY[k] = fLY;
+            fLY = cY;
+        }
         if (POL == 1 && k == K - 1) p.L[K] = cL;
     }
 }
@@ -476,6 +484,7 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float4*
             if (k < K) p.Y[k][q] = 0.f;
         }
         p.L[k] = 0u;
+        if (k < K) p.LY[k] = 0u;
     }
 
     const int y0 = ln.y0, y1 = ln.y1, ny = ln.ny, P = ln.P;
@@ -511,6 +520,7 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float4*
     };
 
     if (V >= 2) {
+        uint32_t prevL = 0u;   // P, code shape 5: label word of the previous level-0 row
         __shared__ float4 ring[kRing][3][32];
         __shared__ uint32_t ring_l[kRing][32];
         auto issue = [&](const int row, const int slot) {
@@ -539,13 +549,23 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float4*
                          ((fL >> 24) < (unsigned)a.s.n_labels),
                      kSiteLabel, a.s.dbg);
             if (kPairShape<V> && POL == 0) fL = pair_offsets(fL);
+            // P, code shape 5: the row's edge label pairs, formed once here
+            // (top edges pair rows t-1 and t, left edges columns q-1 and q)
+            uint32_t fLY = 0u;
+            if (kPairShape<V> && POL == 1) {
+                const uint32_t raw = fL;
+                const uint32_t lNb = __shfl_up_sync(FULL, raw, 1) >> 24;   // column q-1 of lane 0
+                fLY = (((raw << 8) | lNb) << 4) | raw;
+                fL = (prevL << 4) | raw;
+                prevL = raw;
+            }
             fE[0] = e4.x; fE[1] = e4.y; fE[2] = e4.z; fE[3] = e4.w;
             fX[0] = x4.x; fX[1] = x4.y; fX[2] = x4.z; fX[3] = x4.w;
             fY[0] = y4.x; fY[1] = y4.y; fY[2] = y4.z; fY[3] = y4.w;
             issue(t + kRing, slot);
             slot = (slot + 1 == kRing) ? 0 : slot + 1;
-            if (fast) advance<K, false, POL, V>(p, fE, fX, fY, fL, t, a, ln, ringE, ringH, n0);
-            else advance<K, true, POL, V>(p, fE, fX, fY, fL, t, a, ln, ringE, ringH, n0);
+            if (fast) advance<K, false, POL, V>(p, fE, fX, fY, fL, fLY, t, a, ln, ringE, ringH, n0);
+            else advance<K, true, POL, V>(p, fE, fX, fY, fL, fLY, t, a, ln, ringE, ringH, n0);
             finish(t, fE, fX, fY);
         };
         // Two lean rows per loop trip: every pipeline register is replaced
@@ -582,7 +602,7 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float4*
     }
     auto iteration = [&](const int t, const bool fast) {
         float fE[4], fX[4], fY[4];
-        uint32_t fL = nL;
+        uint32_t fL = nL, fLY = 0u;
 #pragma unroll
         for (int q = 0; q < 4; ++q) { fE[q] = nE[q]; fX[q] = nX[q]; fY[q] = nY[q]; }
         if (t + 1 < ny && ln.col_ok) {
@@ -596,8 +616,8 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float4*
             for (int q = 0; q < 4; ++q) { nE[q] = 0.f; nX[q] = 0.f; nY[q] = 0.f; }
             nL = 0u;
         }
-        if (fast) advance<K, false, POL, V>(p, fE, fX, fY, fL, t, a, ln, ringE, ringH, n0);
-        else advance<K, true, POL, V>(p, fE, fX, fY, fL, t, a, ln, ringE, ringH, n0);
+        if (fast) advance<K, false, POL, V>(p, fE, fX, fY, fL, fLY, t, a, ln, ringE, ringH, n0);
+        else advance<K, true, POL, V>(p, fE, fX, fY, fL, fLY, t, a, ln, ringE, ringH, n0);
         finish(t, fE, fX, fY);
     };
     int t = t_begin;
