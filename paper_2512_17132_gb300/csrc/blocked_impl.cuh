@@ -45,6 +45,25 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
+// The four columns of a lane as two register pairs, columns (0, 1) and
+// (2, 3), so that paired FP32 instructions take them without moves; v[q]
+// names column q.
+struct V4 {
+    float2 a, b;
+    __device__ __forceinline__ float& operator[](int q) {
+        return q < 2 ? (q == 0 ? a.x : a.y) : (q == 2 ? b.x : b.y);
+    }
+    __device__ __forceinline__ float operator[](int q) const {
+        return q < 2 ? (q == 0 ? a.x : a.y) : (q == 2 ? b.x : b.y);
+    }
+};
+__device__ __forceinline__ void ld4(const float* p, V4& v) {
+    const float4 x = __ldg(reinterpret_cast<const float4*>(p));
+    v.a = make_float2(x.x, x.y); v.b = make_float2(x.z, x.w);
+}
+__device__ __forceinline__ void st4(float* p, const V4& v) {
+    *reinterpret_cast<float4*>(p) = make_float4(v.a.x, v.a.y, v.b.x, v.b.y);
+}
 __device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
     const float4 x = __ldg(reinterpret_cast<const float4*>(p));
     v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
@@ -80,7 +99,7 @@ constexpr int kRing = 4;   // rows in flight per warp for code shape 2
 // (and, for POL = 1, its label word).
 template <int K>
 struct Pipe {
-    float E[K + 1][4], X[K + 1][4], Y[K][4];
+    V4 E[K + 1], X[K + 1], Y[K];
     uint32_t L[K + 1];
     uint32_t LY[K];   // P, code shape 5: left-edge label pairs of the pending row
 };
@@ -129,8 +148,8 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 // subtraction, so the results are bit for bit those of advance(). The
 // differences along x take a column pair shifted by one and stay scalar.
 template <int K, int V>
-__device__ __forceinline__ void advance_lean_pair(Pipe<K>& p, float (&fE)[4], float (&fX)[4],
-                                                  float (&fY)[4], uint32_t& fL, const Lane& ln,
+__device__ __forceinline__ void advance_lean_pair(Pipe<K>& p, V4& fE, V4& fX,
+                                                  V4& fY, uint32_t& fL, const Lane& ln,
                                                   const BlockedArgs& a, const int t) {
     const float2 S2 = f2(ln.S, ln.S);
     const float2 M1 = f2(-1.0f, -1.0f);
@@ -140,23 +159,23 @@ __device__ __forceinline__ void advance_lean_pair(Pipe<K>& p, float (&fE)[4], fl
         const float4 c01 = pair_at(ln.pair, cL & 0xffffu);
         const float4 c23 = pair_at(ln.pair, cL >> 16);
         const float yR = __shfl_down_sync(FULL, p.Y[k][0], 1);
-        const float2 dhx01 = __ffma2_rn(f2(p.X[k][0], p.X[k][1]), M1, f2(fX[0], fX[1]));
-        const float2 dhx23 = __ffma2_rn(f2(p.X[k][2], p.X[k][3]), M1, f2(fX[2], fX[3]));
+        const float2 dhx01 = __ffma2_rn(p.X[k].a, M1, fX.a);
+        const float2 dhx23 = __ffma2_rn(p.X[k].b, M1, fX.b);
         const float2 dhy01 = f2(__fsub_rn(p.Y[k][1], p.Y[k][0]), __fsub_rn(p.Y[k][2], p.Y[k][1]));
         const float2 dhy23 = f2(__fsub_rn(p.Y[k][3], p.Y[k][2]), __fsub_rn(yR, p.Y[k][3]));
         const float2 e01 = __ffma2_rn(f2(c01.z, c01.w), __fadd2_rn(dhy01, dhx01),
-                                      __fmul2_rn(f2(c01.x, c01.y), f2(p.E[k][0], p.E[k][1])));
+                                      __fmul2_rn(f2(c01.x, c01.y), p.E[k].a));
         const float2 e23 = __ffma2_rn(f2(c23.z, c23.w), __fadd2_rn(dhy23, dhx23),
-                                      __fmul2_rn(f2(c23.x, c23.y), f2(p.E[k][2], p.E[k][3])));
-        const float2 d01 = __ffma2_rn(f2(p.E[k + 1][0], p.E[k + 1][1]), M1, e01);
-        const float2 d23 = __ffma2_rn(f2(p.E[k + 1][2], p.E[k + 1][3]), M1, e23);
-        const float2 x01 = __ffma2_rn(S2, d01, f2(p.X[k][0], p.X[k][1]));
-        const float2 x23 = __ffma2_rn(S2, d23, f2(p.X[k][2], p.X[k][3]));
+                                      __fmul2_rn(f2(c23.x, c23.y), p.E[k].b));
+        const float2 d01 = __ffma2_rn(p.E[k + 1].a, M1, e01);
+        const float2 d23 = __ffma2_rn(p.E[k + 1].b, M1, e23);
+        const float2 x01 = __ffma2_rn(S2, d01, p.X[k].a);
+        const float2 x23 = __ffma2_rn(S2, d23, p.X[k].b);
         const float eL = __shfl_up_sync(FULL, e23.y, 1);
         const float2 dy01 = f2(__fsub_rn(e01.x, eL), __fsub_rn(e01.y, e01.x));
         const float2 dy23 = f2(__fsub_rn(e23.x, e01.y), __fsub_rn(e23.y, e23.x));
-        const float2 y01 = __ffma2_rn(S2, dy01, f2(p.Y[k][0], p.Y[k][1]));
-        const float2 y23 = __ffma2_rn(S2, dy23, f2(p.Y[k][2], p.Y[k][3]));
+        const float2 y01 = __ffma2_rn(S2, dy01, p.Y[k].a);
+        const float2 y23 = __ffma2_rn(S2, dy23, p.Y[k].b);
         if (V == 6 && k + 1 < K) {
             // code shape 6: the state after step k+1 of this row (adjoint tape)
             const int r = t - k - 1;
@@ -169,11 +188,10 @@ __device__ __forceinline__ void advance_lean_pair(Pipe<K>& p, float (&fE)[4], fl
             }
         }
         // level k now waits at row r+1; the new level-(k+1) row r flows up
-#pragma unroll
-        for (int q = 0; q < 4; ++q) { p.E[k][q] = fE[q]; p.X[k][q] = fX[q]; p.Y[k][q] = fY[q]; }
-        fE[0] = e01.x; fE[1] = e01.y; fE[2] = e23.x; fE[3] = e23.y;
-        fX[0] = x01.x; fX[1] = x01.y; fX[2] = x23.x; fX[3] = x23.y;
-        fY[0] = y01.x; fY[1] = y01.y; fY[2] = y23.x; fY[3] = y23.y;
+        p.E[k] = fE; p.X[k] = fX; p.Y[k] = fY;
+        fE.a = e01; fE.b = e23;
+        fX.a = x01; fX.b = x23;
+        fY.a = y01; fY.b = y23;
         p.L[k] = fL;
         fL = cL;
     }
@@ -185,8 +203,8 @@ __device__ __forceinline__ void advance_lean_pair(Pipe<K>& p, float (&fE)[4], fl
 // exactly) and the lossy edge updates keep their per-edge label-pair
 // coefficients (scalar). Bit for bit the results of advance().
 template <int K>
-__device__ __forceinline__ void advance_lean_pair_p(Pipe<K>& p, float (&fE)[4], float (&fX)[4],
-                                                    float (&fY)[4], uint32_t& fL, uint32_t& fLY,
+__device__ __forceinline__ void advance_lean_pair_p(Pipe<K>& p, V4& fE, V4& fX,
+                                                    V4& fY, uint32_t& fL, uint32_t& fLY,
                                                     const Lane& ln) {
     const float2 S2 = f2(ln.S, ln.S);
     const float2 M1 = f2(-1.0f, -1.0f);
@@ -195,14 +213,14 @@ __device__ __forceinline__ void advance_lean_pair_p(Pipe<K>& p, float (&fE)[4], 
         // the row's edge label pairs, formed once when the row was loaded
         const uint32_t xP = p.L[k], yP = p.LY[k];
         const float yR = __shfl_down_sync(FULL, p.Y[k][0], 1);
-        const float2 dhx01 = __ffma2_rn(f2(p.X[k][0], p.X[k][1]), M1, f2(fX[0], fX[1]));
-        const float2 dhx23 = __ffma2_rn(f2(p.X[k][2], p.X[k][3]), M1, f2(fX[2], fX[3]));
+        const float2 dhx01 = __ffma2_rn(p.X[k].a, M1, fX.a);
+        const float2 dhx23 = __ffma2_rn(p.X[k].b, M1, fX.b);
         const float2 dhy01 = f2(__fsub_rn(p.Y[k][1], p.Y[k][0]), __fsub_rn(p.Y[k][2], p.Y[k][1]));
         const float2 dhy23 = f2(__fsub_rn(p.Y[k][3], p.Y[k][2]), __fsub_rn(yR, p.Y[k][3]));
-        const float2 e01 = __ffma2_rn(S2, __fadd2_rn(dhy01, dhx01), f2(p.E[k][0], p.E[k][1]));
-        const float2 e23 = __ffma2_rn(S2, __fadd2_rn(dhy23, dhx23), f2(p.E[k][2], p.E[k][3]));
-        const float2 d01 = __ffma2_rn(f2(p.E[k + 1][0], p.E[k + 1][1]), M1, e01);
-        const float2 d23 = __ffma2_rn(f2(p.E[k + 1][2], p.E[k + 1][3]), M1, e23);
+        const float2 e01 = __ffma2_rn(S2, __fadd2_rn(dhy01, dhx01), p.E[k].a);
+        const float2 e23 = __ffma2_rn(S2, __fadd2_rn(dhy23, dhx23), p.E[k].b);
+        const float2 d01 = __ffma2_rn(p.E[k + 1].a, M1, e01);
+        const float2 d23 = __ffma2_rn(p.E[k + 1].b, M1, e23);
         const float oE[4] = {e01.x, e01.y, e23.x, e23.y};
         const float d[4] = {d01.x, d01.y, d23.x, d23.y};
         float oX[4], oY[4];
@@ -235,8 +253,8 @@ __device__ __forceinline__ void advance_lean_pair_p(Pipe<K>& p, float (&fE)[4], 
 // CPML, source, monitor or boundary row and lie inside the valid range;
 // both paths round identically.
 template <int K, bool GENERAL, int POL, int V>
-__device__ __forceinline__ void advance(Pipe<K>& p, float (&fE)[4], float (&fX)[4],
-                                        float (&fY)[4], uint32_t& fL, uint32_t& fLY, const int t,
+__device__ __forceinline__ void advance(Pipe<K>& p, V4& fE, V4& fX,
+                                        V4& fY, uint32_t& fL, uint32_t& fLY, const int t,
                                         const BlockedArgs& a, const Lane& ln, float4* ringE,
                                         float4* ringH, const int64_t n0) {
     if constexpr (!GENERAL && kPairShape<V> && POL == 0) {
@@ -506,7 +524,7 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float4*
         return f;
     };
 
-    auto finish = [&](const int t, float (&fE)[4], float (&fX)[4], float (&fY)[4]) {
+    auto finish = [&](const int t, V4& fE, V4& fX, V4& fY) {
         const int ro = t - K;
         if (ln.own && ro >= y0 && ro < y1 &&
             index_ok(ro >= 0 && ro < ny, kSiteStoreRow, a.s.dbg)) {
@@ -539,7 +557,7 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float4*
         int slot = 0;
         auto row = [&](const int t, const bool fast) {
             cp_async_wait<kRing - 1>();
-            float fE[4], fX[4], fY[4];
+            V4 fE, fX, fY;
             const float4 e4 = ring[slot][0][lane], x4 = ring[slot][1][lane], y4 = ring[slot][2][lane];
             uint32_t fL = ring_l[slot][lane];
             // every label must index the coefficient table (debug builds)
@@ -601,7 +619,7 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float4*
         for (int q = 0; q < 4; ++q) { nE[q] = 0.f; nX[q] = 0.f; nY[q] = 0.f; }
     }
     auto iteration = [&](const int t, const bool fast) {
-        float fE[4], fX[4], fY[4];
+        V4 fE, fX, fY;
         uint32_t fL = nL, fLY = 0u;
 #pragma unroll
         for (int q = 0; q < 4; ++q) { fE[q] = nE[q]; fX[q] = nX[q]; fY[q] = nY[q]; }
