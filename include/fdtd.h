@@ -138,9 +138,9 @@ typedef struct fdtd_stats {
                                   prefetch, 1 two rows per trip, 2 rows streamed through a
                                   shared-memory ring by cp.async, two lean rows per trip, 3 the
                                   ring with one row per trip, built under a 224-register cap,
-                                  5 shape 2 with a label-pair coefficient table and paired FP32
-                                  instructions (S polarisation, at most 16 labels). Default: 5
-                                  where allowed, else 2; P handles run shapes 2 and 3; 4 is
+                                  5 shape 2 with paired FP32 instructions (at most 16 labels;
+                                  S adds a label-pair coefficient table). Default: 5 where
+                                  allowed, else 2; P handles run shapes 2, 3 and 5; 4 and 6 are
                                   internal (EINVAL) */
 #define FDTD_OPT_GRAPH 7       /* batches: replay captured CUDA graphs of launch chunks (default 1) */
 #define FDTD_OPT_PLAN_WEIGHT 8 /* segment planner: cost of a general-path iteration of the blocked
