@@ -287,6 +287,14 @@ def event_seconds(ev0, ev1, wall):
     return wall, "CUDA-synchronised wall clock (events did not span the work)"
 
 
+def finite_or_none(x):
+    """x as a float, or None where it is not finite (R and T of a run too
+    short for the pulse to reach the monitors), so that the line stays
+    strict JSON."""
+    x = float(x)
+    return x if math.isfinite(x) else None
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     for f in ("blocked_impl.cuh", "blocked_s.cu", "fdtd_device.cuh"):
@@ -807,8 +815,8 @@ def main():
             "roofline": roofline_record(achieved, peak, peak_kind, algo_bytes, avg_launch_s,
                                         traffic, inst, clk),
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches),
-            "rt_last": {"lambda_nm": results[-1][0] * 1e9, "R": results[-1][1][0],
-                        "T": results[-1][1][1]},
+            "rt_last": {"lambda_nm": results[-1][0] * 1e9, "R": finite_or_none(results[-1][1][0]),
+                        "T": finite_or_none(results[-1][1][1])},
             "rt_check": rt_check,
             "adjoint": adjoint,
         }
