@@ -279,10 +279,12 @@ void fdtd_destroy(fdtd_handle* h);
  * per cell (ny*nx doubles each, host or device, NULL to skip) and, for
  * labelled handles, dJ/dn and dJ/dk per label (n_labels pairs, host or
  * device, NULL to skip); out = {J, R, T} (may be NULL). Segment by segment
- * (last first) the states are recomputed from their checkpoint into a device
- * tape of `every` states (about 12*every bytes per cell, freed on return)
- * and the transpose of every update is applied in reverse order; per-segment
- * FP32 sums are accumulated in FP64. The handle keeps its final forward
+ * (last first) the steps are recomputed from their checkpoint, storing for
+ * each step the two forward factors of the gradient sums (Ez before the
+ * update and the factor of cb in it) on a device tape (about 8*every bytes
+ * per cell plus two states, freed on return), and the transpose of every
+ * update is applied in reverse order; per-segment FP32 sums are accumulated
+ * in FP64. The handle keeps its final forward
  * state. FDTD_ESTATE if no checkpointed run precedes or no incident power
  * reached t_row; FDTD_EINVAL for P-polarised handles (the adjoint covers
  * the S case). Synchronises. */

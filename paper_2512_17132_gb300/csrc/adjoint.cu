@@ -3,10 +3,13 @@
 //
 // fdtd_forward_checkpointed runs the forward loop from step 0 and stores the
 // full state every C steps on the device. fdtd_backward then walks the
-// segments last to first: it recomputes the segment's states from its
-// checkpoint into a device tape (the forward arithmetic exactly, so the tape
-// holds the states the forward run produced) and applies, step by step in
-// reverse, the transpose of every update of the leapfrog step:
+// segments last to first: it recomputes the segment from its checkpoint
+// (the forward arithmetic exactly, so the same bits as the forward run) and
+// stores on a device tape, for every step n, the two factors that the
+// gradient sums take from the forward run: Ez^{n-1/2} and the factor of cb
+// in the Ez update (curl^n with its CPML and TF/SF terms), 8 bytes per cell
+// and step. It then applies, step by step in reverse, the transpose of every
+// update of the leapfrog step:
 //
 //   forward step n                         reverse step n
 //   Ez <- ca Ez + cb curl(H, psi_E)        k_adj_h: H monitor sources, transposes
@@ -15,8 +18,9 @@
 //                                          Ez^{n-1/2}, gcb += lE curl^n, transpose
 //                                          of the E update (psi_E carry), ca lE
 //
-// Each reverse kernel recomputes the neighbour terms it needs instead of
-// staging them, so the adjoint of Ez and the CPML carries are ping-ponged.
+// Each reverse kernel recomputes the adjoint neighbour terms it needs
+// instead of staging them, so the adjoint of Ez and the CPML carries are
+// ping-ponged.
 // Where rows split into float4s (nx % 4 == 0) the reverse kernels take four
 // columns per thread (k_adj_h4, k_adj_e4); the scalar kernels serve the
 // other widths; both give the same bits.
@@ -61,7 +65,6 @@ struct AdjArgs {
     const float2* cellcoef;
     const float* pml_e;
     const float* pml_h;
-    const float* hinc;
     const double2* phE;
     const double2* phH;
     const double2* dft;     // final DFT sums [4][nx]
@@ -69,7 +72,7 @@ struct AdjArgs {
     float* lE;              // adjoint of Ez (the buffer the H reverse updates)
     float* lX; float* lY;
     float* gA; float* gB;   // FP32 per-segment sums
-    const float* tE; const float* tX; const float* tY; const float* tPE;   // tape state of step n
+    const float* tE; const float* tC;   // tape of step n: Ez^{n-1/2}, factor of cb
     int n_coef;             // entries of coef (labelled handles)
     int64_t n_tab;          // table entries valid on the device (debug index checks)
     unsigned* dbg;          // error word of the debug index checks
@@ -175,25 +178,11 @@ __global__ void k_adj_e(AdjArgs a, int64_t n, const float* __restrict__ lE_in,
     const int j = blockIdx.y;
     if (i >= a.nx) return;
     const size_t o = (size_t)j * a.pitch + i;
-    const int ir = (i + 1 == a.nx) ? 0 : i + 1;
     const int il = (i == 0) ? a.nx - 1 : i - 1;
     const float eb = lE_in[o];
-    // forward curl of step n from the taped state (same rounding as forward)
-    const float dhy = __fsub_rn(a.tY[(size_t)j * a.pitch + ir], a.tY[o]);
-    const float hxb = (j + 1 < a.ny) ? a.tX[o + a.pitch] : 0.0f;
-    float dhx = __fsub_rn(hxb, a.tX[o]);
-    if (j == a.js) dhx = __fsub_rn(dhx, tab_n(a.hinc, n, a.n_tab, a.dbg));
-    const int pe = pml_e_index(j, a.ny, a.P);
-    float curl;
-    if (pe >= 0) {
-        const float b = a.pml_e[pe], cc = a.pml_e[2 * a.P + pe], ik = a.pml_e[4 * a.P + pe];
-        const float psi = psi_new(b, cc, a.tPE[(size_t)pe * a.pitch + i], dhx);
-        curl = __fadd_rn(dhy, __fmaf_rn(dhx, ik, psi));
-    } else {
-        curl = __fadd_rn(dhy, dhx);
-    }
+    // gradient sums with the taped factors of step n
     a.gA[o] = __fmaf_rn(eb, a.tE[o], a.gA[o]);
-    a.gB[o] = __fmaf_rn(eb, curl, a.gB[o]);
+    a.gB[o] = __fmaf_rn(eb, a.tC[o], a.gB[o]);
     float c0, g0, cl, gu = 0.f, dummy;
     adj_curl(a, j, i, lE_in, mE_in, mE_out, &c0, &g0);
     adj_curl(a, j, il, lE_in, mE_in, nullptr, &cl, &dummy);
@@ -340,38 +329,13 @@ __global__ void __launch_bounds__(256) k_adj_e4(AdjArgs a, int64_t n, const floa
     const int j = blockIdx.y;
     if (i0 >= a.nx) return;
     const size_t o = (size_t)j * a.pitch + i0;
-    const int ir = (i0 + 4 == a.nx) ? 0 : i0 + 4;
     const int il = (i0 == 0) ? a.nx - 1 : i0 - 1;
     float eb[4];
     ld4v(lE_in + o, eb);
-    // forward curl of step n from the taped state (same rounding as forward)
-    float ty[5], x0[4], x1[4], te[4], curl[4];
-    ld4v(a.tY + o, *reinterpret_cast<float (*)[4]>(ty));
-    ty[4] = a.tY[(size_t)j * a.pitch + ir];
-    ld4v(a.tX + o, x0);
-    if (j + 1 < a.ny) {
-        ld4v(a.tX + o + a.pitch, x1);
-    } else {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) x1[q] = 0.0f;
-    }
+    // the taped factors of step n
+    float te[4], curl[4];
     ld4v(a.tE + o, te);
-    const int pe = pml_e_index(j, a.ny, a.P);
-    float psi_old[4];
-    if (pe >= 0) ld4v(a.tPE + (size_t)pe * a.pitch + i0, psi_old);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const float dhy = __fsub_rn(ty[q + 1], ty[q]);
-        float dhx = __fsub_rn(x1[q], x0[q]);
-        if (j == a.js) dhx = __fsub_rn(dhx, tab_n(a.hinc, n, a.n_tab, a.dbg));
-        if (pe >= 0) {
-            const float b = a.pml_e[pe], cc = a.pml_e[2 * a.P + pe], ik = a.pml_e[4 * a.P + pe];
-            const float psi = psi_new(b, cc, psi_old[q], dhx);
-            curl[q] = __fadd_rn(dhy, __fmaf_rn(dhx, ik, psi));
-        } else {
-            curl[q] = __fadd_rn(dhy, dhx);
-        }
-    }
+    ld4v(a.tC + o, curl);
     float gA[4], gB[4];
     ld4v(a.gA + o, gA);
     ld4v(a.gB + o, gB);
@@ -489,9 +453,8 @@ __global__ void k_adj_chain(ChainArgs a) {
 // iteration t from its input rows r and r + 1. Only level 0's input (the
 // adjoint state lE, lX, lY) is read from memory and only level K's output
 // written; the adjoint CPML carries travel between levels in a per-warp
-// shared-memory ring; every level reads the taped forward state of its step
-// (Ez, Hy of row r, Hx of row r + 1; Hx of row r is kept from the previous
-// iteration). Each cell's gradient sums are read, updated and written by
+// shared-memory ring; every level reads the taped gradient factors of its
+// step for its output row r. Each cell's gradient sums are read, updated and written by
 // the one lane that owns it, level after level, so they accumulate in the
 // same order as with one reverse step per launch. Every expression is that
 // of k_adj_h4 / k_adj_e4, so the gradients are bit for bit the same.
@@ -501,9 +464,9 @@ struct AdjBlockArgs {
     float* lE_out; float* lX_out; float* lY_out;
     const float* mE_in; const float* mH_in;
     float* mE_out; float* mH_out;
-    float* const* tape;                 // tape state base pointers; level k uses tape[m_top - k]
+    float* const* tape;                 // tape step base pointers; level k uses tape[m_top - k]
     int m_top;
-    size_t tape_f;                      // floats per field of a tape state (pitch * ny)
+    size_t tape_f;                      // floats per plane of a tape step (pitch * ny)
     const int* seg_y0;
     int n_strips, n_tasks, w_int;
 };
@@ -514,20 +477,16 @@ __device__ __forceinline__ void ld4g(const float* p, float (&v)[4]) {
     const float4 x = __ldg(reinterpret_cast<const float4*>(p));
     v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
 }
-__device__ __forceinline__ void ld4c(const float* p, float (&v)[4]) {   // written in this kernel
-    const float4 x = *reinterpret_cast<const float4*>(p);
-    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
-}
 __device__ __forceinline__ void st4g(float* p, const float (&v)[4]) {
     *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
 // Per-level pipeline registers: the level's pending input row r (lE, lX,
-// lY and its label word), adj_dez of row r, g0 (the E-transpose term) of row
-// r - 1, and the taped Hx of row r.
+// lY and its label word), adj_dez of row r and g0 (the E-transpose term) of
+// row r - 1.
 template <int K>
 struct AdjPipe {
-    float E[K][4], X[K][4], Y[K][4], D[K][4], G[K][4], TX[K][4];
+    float E[K][4], X[K][4], Y[K][4], D[K][4], G[K][4];
     float GA[K][4], GB[K][4];           // running gradient sums of the pending row
     uint32_t L[K];
 };
@@ -545,8 +504,8 @@ struct AdjLane {
 template <int K, bool GENERAL>
 __device__ __forceinline__ void adj_level(const AdjBlockArgs& b, const float2* s_coef,
                                           AdjPipe<K>& p, const int k, const int t,
-                                          const int64_t n_top, const float* tb,
-                                          const float4* tslot, float (&iE)[4], float (&iX)[4],
+                                          const int64_t n_top, const float4* tslot,
+                                          float (&iE)[4], float (&iX)[4],
                                           float (&iY)[4], float (&iA)[4], float (&iB)[4],
                                           uint32_t& iL, const AdjLane& ln, float4* ringE,
                                           float4* ringH) {
@@ -556,15 +515,6 @@ __device__ __forceinline__ void adj_level(const AdjBlockArgs& b, const float2* s
     const float S = a.S;
     const size_t pitch = (size_t)a.pitch;
     const bool r_ok = !GENERAL || (r >= 0 && r < ln.ny);
-    // taped forward state of step n (Ez, Hy of row r, Hx of row q), staged in
-    // shared memory one iteration ahead (zero outside the grid: Hx[ny] = 0)
-    float tE[4], tY[4], tXq[4];
-    {
-        const float4 e4 = tslot[0], y4 = tslot[32], x4 = tslot[64];
-        tE[0] = e4.x; tE[1] = e4.y; tE[2] = e4.z; tE[3] = e4.w;
-        tY[0] = y4.x; tY[1] = y4.y; tY[2] = y4.z; tY[3] = y4.w;
-        tXq[0] = x4.x; tXq[1] = x4.y; tXq[2] = x4.z; tXq[3] = x4.w;
-    }
     // 1. transpose of the Hx update at edge q (adj_dez), psi_H carry of row q
     float dq[4];
     if (!GENERAL) {
@@ -620,33 +570,19 @@ __device__ __forceinline__ void adj_level(const AdjBlockArgs& b, const float2* s
         if (GENERAL && (r == a.jr || r == a.jt))
 #pragma unroll
             for (int c = 0; c < 4; ++c) eh[c] = __fadd_rn(eh[c], src_e(a, r, ln.gx + c, n));
-        // 3. the forward curl of step n from the tape (forward rounding)
-        const float tyR = __shfl_down_sync(kFull, tY[0], 1);
-        float curl[4];
-        const int pe = GENERAL ? pml_e_index(r, ln.ny, ln.P) : -1;
-        float psi_old[4];
-        if (GENERAL && pe >= 0) ld4g(tb + 3 * b.tape_f + (size_t)pe * pitch + ln.gx, psi_old);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const float dhy = __fsub_rn(c < 3 ? tY[c + 1] : tyR, tY[c]);
-            float dhx = __fsub_rn(tXq[c], p.TX[k][c]);
-            if (GENERAL && r == a.js) dhx = __fsub_rn(dhx, tab_n(a.hinc, n, a.n_tab, a.dbg));
-            if (GENERAL && pe >= 0) {
-                const float bb = a.pml_e[pe], cc = a.pml_e[2 * a.P + pe], ik = a.pml_e[4 * a.P + pe];
-                const float psi = psi_new(bb, cc, psi_old[c], dhx);
-                curl[c] = __fadd_rn(dhy, __fmaf_rn(dhx, ik, psi));
-            } else {
-                curl[c] = __fadd_rn(dhy, dhx);
-            }
-        }
-        // 4. gradient sums: they travel with the row from level to level (read
-        // by level 0, written after level K - 1), level order = step order
+        // 3. gradient sums with the taped factors of step n, row r (staged in
+        // shared memory one iteration ahead); the sums travel with the row
+        // from level to level (read by level 0, written after level K - 1),
+        // level order = step order
+        const float4 te = tslot[0], tc = tslot[32];
+        const float tE[4] = {te.x, te.y, te.z, te.w}, curl[4] = {tc.x, tc.y, tc.z, tc.w};
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             oA[c] = __fmaf_rn(eh[c], tE[c], p.GA[k][c]);
             oB[c] = __fmaf_rn(eh[c], curl[c], p.GB[k][c]);
         }
-        // 5. transpose of the Ez update (adj_curl of row r), psi_E carry of row r
+        const int pe = GENERAL ? pml_e_index(r, ln.ny, ln.P) : -1;
+        // 4. transpose of the Ez update (adj_curl of row r), psi_E carry of row r
         const uint32_t L = p.L[k];
         float2 cf[4];
 #pragma unroll
@@ -702,7 +638,7 @@ __device__ __forceinline__ void adj_level(const AdjBlockArgs& b, const float2* s
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         p.E[k][c] = iE[c]; p.X[k][c] = iX[c]; p.Y[k][c] = iY[c];
-        p.D[k][c] = dq[c]; p.G[k][c] = g0[c]; p.TX[k][c] = tXq[c];
+        p.D[k][c] = dq[c]; p.G[k][c] = g0[c];
         p.GA[k][c] = iA[c]; p.GB[k][c] = iB[c];
         iE[c] = oE[c]; iX[c] = oX[c]; iY[c] = oY[c]; iA[c] = oA[c]; iB[c] = oB[c];
     }
@@ -723,8 +659,8 @@ __global__ void __launch_bounds__(32) k_adj_blocked(const AdjBlockArgs b, const 
     __shared__ float2 s_coef[256];
     __shared__ float4 s_ring[2][K][32];
     // tape rows of each level, kAdjRing iterations in flight:
-    // [slot][level][Ez, Hy, Hx][lane]
-    __shared__ float4 s_tape[kAdjRing][K][3][32];
+    // [slot][level][Ez^{n-1/2}, factor of cb][lane]
+    __shared__ float4 s_tape[kAdjRing][K][2][32];
     // level-0 input row (lE, lX, lY, gA, gB) and its labels, same slots
     __shared__ float4 s_in[kAdjRing][5][32];
     __shared__ uint32_t s_lab[kAdjRing][32];
@@ -747,7 +683,7 @@ __global__ void __launch_bounds__(32) k_adj_blocked(const AdjBlockArgs b, const 
     ln.own = (xl >= H) && (xl < H + b.w_int) && (xg_pre < ln.nx) && col_ok;
     float4* ringE = &s_ring[0][0][lane];
     float4* ringH = &s_ring[1][0][lane];
-    const float* tbs[K];                 // tape state of each level's step
+    const float* tbs[K];                 // tape step of each level
 #pragma unroll
     for (int k = 0; k < K; ++k) tbs[k] = b.tape[b.m_top - k];
     AdjPipe<K> p;
@@ -756,7 +692,7 @@ __global__ void __launch_bounds__(32) k_adj_blocked(const AdjBlockArgs b, const 
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             p.E[k][c] = 0.f; p.X[k][c] = 0.f; p.Y[k][c] = 0.f;
-            p.D[k][c] = 0.f; p.G[k][c] = 0.f; p.TX[k][c] = 0.f;
+            p.D[k][c] = 0.f; p.G[k][c] = 0.f;
             p.GA[k][c] = 0.f; p.GB[k][c] = 0.f;
         }
         p.L[k] = 0u;
@@ -773,22 +709,20 @@ __global__ void __launch_bounds__(32) k_adj_blocked(const AdjBlockArgs b, const 
         for (int s = 0; s < 5; ++s) f = f && ((unsigned)(t - sp[s]) > (unsigned)K);
         return f;
     };
-    // tape rows needed at iteration t: level k reads Ez, Hy of row t - k - 1 and
-    // Hx of row t - k of its step; rows outside the grid are zero-filled
+    // tape rows needed at iteration t: level k reads both factors of row
+    // t - k - 1 of its step; rows outside the grid are zero-filled
     float4* tape_lane = &s_tape[0][0][0][lane];
     auto stage_tape = [&](int t) {
         const int slot = t % kAdjRing;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            const int r = t - k - 1, q = t - k;
-            const bool rok = r >= 0 && r < ny && col_ok, qok = q >= 0 && q < ny && col_ok;
+            const int r = t - k - 1;
+            const bool rok = r >= 0 && r < ny && col_ok;
             const float* tb = tbs[k];
             const size_t orow = (size_t)(rok ? r : 0) * pitch + ln.gx;
-            const size_t oq = (size_t)(qok ? q : 0) * pitch + ln.gx;
-            float4* dst = tape_lane + (slot * K + k) * 96;
+            float4* dst = tape_lane + (slot * K + k) * 64;
             cp16(dst, tb + orow, rok ? 16 : 0);
-            cp16(dst + 32, tb + 2 * b.tape_f + orow, rok ? 16 : 0);
-            cp16(dst + 64, tb + b.tape_f + oq, qok ? 16 : 0);
+            cp16(dst + 32, tb + b.tape_f + orow, rok ? 16 : 0);
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
@@ -832,17 +766,17 @@ __global__ void __launch_bounds__(32) k_adj_blocked(const AdjBlockArgs b, const 
             }
         }
         uint32_t iL = s_lab[t % kAdjRing][lane];
-        const float4* ts = tape_lane + (t % kAdjRing) * K * 96;
+        const float4* ts = tape_lane + (t % kAdjRing) * K * 64;
         if (is_lean(t)) {
 #pragma unroll
             for (int k = 0; k < K; ++k)
-                adj_level<K, false>(b, s_coef, p, k, t, n_top, tbs[k], ts + k * 96, iE, iX, iY, iA,
-                                    iB, iL, ln, ringE, ringH);
+                adj_level<K, false>(b, s_coef, p, k, t, n_top, ts + k * 64, iE, iX, iY, iA, iB,
+                                    iL, ln, ringE, ringH);
         } else {
 #pragma unroll
             for (int k = 0; k < K; ++k)
-                adj_level<K, true>(b, s_coef, p, k, t, n_top, tbs[k], ts + k * 96, iE, iX, iY, iA,
-                                   iB, iL, ln, ringE, ringH);
+                adj_level<K, true>(b, s_coef, p, k, t, n_top, ts + k * 64, iE, iX, iY, iA, iB,
+                                   iL, ln, ringE, ringH);
         }
         const int ro = t - K;
         if (ln.own && ro >= ln.y0 && ro < ln.y1) {
@@ -940,43 +874,30 @@ void copy_state_out(fdtd_handle* h, float* dst) {
     ACK(cudaMemcpyAsync(v.PH, h->psiH[c], p, cudaMemcpyDeviceToDevice, h->stream));
 }
 
-// One forward step n from state `in` to state `out` (no monitor sums).
-void step_out_of_place(fdtd_handle* h, const StateView& in, const StateView& out, int64_t n,
-                       double2* dummy) {
+// One forward step n from state `in` to state `out` (no monitor sums) with
+// the per-step kernels, storing the step's gradient factors at `tape`
+// (grids that the blocked kernel does not take: per-cell materials or
+// nx % 4 != 0).
+void step_to_tape(fdtd_handle* h, const StateView& in, const StateView& out, int64_t n,
+                  float* tape, double2* dummy) {
     StepArgs s = step_args(h);
     s.dft = dummy;
     const size_t f = (size_t)h->pitch * h->g.ny * sizeof(float);
     const size_t p = (size_t)std::max(2 * h->g.pml_cells, 1) * h->pitch * sizeof(float);
-    if (!h->maps && h->g.nx % 4 == 0) {
-        BlockPlan* pl = nullptr;
-        for (auto& q : h->plans)
-            if (q.K == 1 && q.d_seg_y0) pl = &q;
-        if (pl) {
-            BlockedArgs b{};
-            b.s = s;
-            b.ez_in = in.E; b.hx_in = in.X; b.hy_in = in.Y;
-            b.ez_out = out.E; b.hx_out = out.X; b.hy_out = out.Y;
-            b.psiE_in = in.PE; b.psiH_in = in.PH; b.psiE_out = out.PE; b.psiH_out = out.PH;
-            b.seg_y0 = pl->d_seg_y0;
-            b.n_strips = pl->n_strips;
-            b.n_tasks = pl->n_strips * pl->n_segs;
-            b.w_int = pl->w_int;
-            launch_blocked(b, 1, h->opt_variant, n, h->stream);
-            return;
-        }
-    }
     ACK(cudaMemcpyAsync(out.E, in.E, f, cudaMemcpyDeviceToDevice, h->stream));
     ACK(cudaMemcpyAsync(out.X, in.X, f, cudaMemcpyDeviceToDevice, h->stream));
     ACK(cudaMemcpyAsync(out.Y, in.Y, f, cudaMemcpyDeviceToDevice, h->stream));
     ACK(cudaMemcpyAsync(out.PE, in.PE, p, cudaMemcpyDeviceToDevice, h->stream));
     ACK(cudaMemcpyAsync(out.PH, in.PH, p, cudaMemcpyDeviceToDevice, h->stream));
-    launch_naive_step(s, out.E, out.X, out.Y, out.PE, out.PH, n, h->stream);
+    launch_naive_step(s, out.E, out.X, out.Y, out.PE, out.PH, n, h->stream, tape,
+                      (size_t)h->pitch * h->g.ny);
 }
 
 // Recompute K steps n..n+K-1 from state `in` in one blocked launch (code
-// shape 6, or 4 for more than 16 labels): the launch writes the final state to `out` and the states after
-// the intermediate steps to tape_ptrs[0..K-2] (device array of state base
-// pointers); the same arithmetic as K one-step launches, so the same bits.
+// shape 6, or 4 for more than 16 labels): the launch writes the final state
+// to `out` and the gradient factors of step n+k to tape_ptrs[k] (device
+// array of tape step base pointers); the same arithmetic as K one-step
+// launches, so the same bits.
 void steps_to_tape(fdtd_handle* h, const StateView& in, const StateView& out, int K, int64_t n,
                    float* const* tape_ptrs, double2* dummy) {
     StepArgs s = step_args(h);
@@ -1048,6 +969,7 @@ int fdtd_backward(fdtd_handle* h, double wR, double wT, double* g_eps, double* g
     if (!h) return FDTD_EINVAL;
     std::vector<float*> tape;
     std::vector<AdjPlan> adj_plans;
+    float* st[2] = {nullptr, nullptr};
     float* buf = nullptr;
     double* dbl = nullptr;
     double2* dummy = nullptr;
@@ -1056,6 +978,7 @@ int fdtd_backward(fdtd_handle* h, double wR, double wT, double* g_eps, double* g
         for (auto& pl : adj_plans) if (pl.d_seg) cudaFree(pl.d_seg);
         if (d_tape_ptrs) cudaFree(d_tape_ptrs);
         for (auto& t : tape) cudaFree(t);
+        for (float* q : st) if (q) cudaFree(q);
         if (buf) cudaFree(buf);
         if (dbl) cudaFree(dbl);
         if (dummy) cudaFree(dummy);
@@ -1083,18 +1006,14 @@ int fdtd_backward(fdtd_handle* h, double wR, double wT, double* g_eps, double* g
         const size_t pr = (size_t)std::max(2 * g.pml_cells, 1) * pitch;
         const int every = h->adj_every;
         const int64_t steps = h->adj_steps;
-        if (!h->maps && nx % 4 == 0) {
-            // segment plan and scratch of the one-step blocked kernel used to recompute
-            const int keep = h->opt_seg;
-            h->opt_seg = 0;
-            get_plan(h, 1);
-            h->opt_seg = keep;
-        }
+        // the tape: per step of a segment, Ez^{n-1/2} and the factor of cb
+        // (f floats each); two state buffers carry the recompute
         const size_t sf = state_floats(h);
         tape.assign((size_t)std::min<int64_t>(every, steps), nullptr);
-        for (auto& t : tape) ACK(cudaMalloc(&t, sf * sizeof(float)));
+        for (auto& t : tape) ACK(cudaMalloc(&t, 2 * f * sizeof(float)));
+        for (float*& q : st) ACK(cudaMalloc(&q, sf * sizeof(float)));
         // multi-step recompute (labelled grids with nx % 4 == 0): a device
-        // array of the tape states' base pointers
+        // array of the tape steps' base pointers
         const bool multi = !h->maps && nx % 4 == 0;
         if (multi) {
             ACK(cudaMalloc(&d_tape_ptrs, tape.size() * sizeof(float*)));
@@ -1112,7 +1031,7 @@ int fdtd_backward(fdtd_handle* h, double wR, double wT, double* g_eps, double* g
         a.nx = nx; a.ny = ny; a.pitch = pitch; a.lpitch = h->lpitch; a.P = g.pml_cells;
         a.js = g.tfsf_row; a.jr = g.r_row; a.jt = g.t_row; a.S = (float)h->S;
         a.labels = h->labels; a.coef = h->coef; a.cellcoef = h->cellcoef;
-        a.pml_e = h->pml_e; a.pml_h = h->pml_h; a.hinc = h->d_hinc;
+        a.pml_e = h->pml_e; a.pml_h = h->pml_h;
         a.phE = h->d_phE; a.phH = h->d_phH; a.dft = h->dft;
         a.kR = wR / (-(double)nx * s0);
         a.kT = wT / ((double)nx * s0);
@@ -1139,20 +1058,28 @@ int fdtd_backward(fdtd_handle* h, double wR, double wT, double* g_eps, double* g
         for (int64_t c = n_seg - 1; c >= 0; --c) {
             const int64_t c0 = c * every;
             const int L = (int)std::min<int64_t>(every, steps - c0);
-            ACK(cudaMemcpyAsync(tape[0], h->ck[(size_t)c], sf * sizeof(float),
-                                cudaMemcpyDeviceToDevice, h->stream));
+            // recompute steps c0 .. c0+L-1 from the checkpoint (read only)
+            StateView in = view(h, h->ck[(size_t)c]);
+            int so = 0;
             if (multi) {
                 const int Kmax = std::min(std::max(h->opt_block, 1), blocked_max_K());
-                for (int m = 0; m + 1 < L;) {
-                    const int Kr = std::min(Kmax, L - 1 - m);
-                    steps_to_tape(h, view(h, tape[m]), view(h, tape[m + Kr]), Kr, c0 + m,
-                                  d_tape_ptrs + m + 1, dummy);
+                for (int m = 0; m < L;) {
+                    const int Kr = std::min(Kmax, L - m);
+                    const StateView out = view(h, st[so]);
+                    steps_to_tape(h, in, out, Kr, c0 + m, d_tape_ptrs + m, dummy);
                     h->total_launches += 1;
+                    in = out;
+                    so ^= 1;
                     m += Kr;
                 }
             } else {
-                for (int m = 0; m + 1 < L; ++m)
-                    step_out_of_place(h, view(h, tape[m]), view(h, tape[m + 1]), c0 + m, dummy);
+                for (int m = 0; m < L; ++m) {
+                    const StateView out = view(h, st[so]);
+                    step_to_tape(h, in, out, c0 + m, tape[m], dummy);
+                    h->total_launches += 3;
+                    in = out;
+                    so ^= 1;
+                }
             }
             for (int m_top = L - 1; kb > 0 && m_top >= 0;) {
                 const int Kr = std::min(kb, m_top + 1);
@@ -1188,8 +1115,8 @@ int fdtd_backward(fdtd_handle* h, double wR, double wT, double* g_eps, double* g
             }
             for (int m = L - 1; kb == 0 && m >= 0; --m) {
                 const int64_t n = c0 + m;
-                const StateView v = view(h, tape[m]);
-                a.tE = v.E; a.tX = v.X; a.tY = v.Y; a.tPE = v.PE;
+                a.tE = tape[m];
+                a.tC = tape[m] + f;
                 a.lE = lEb[le_cur];
                 if (vec4) {
                     k_adj_h4<<<grd4, blk, 0, h->stream>>>(a, n, mHb[ph_cur], mHb[ph_cur ^ 1]);

@@ -125,11 +125,12 @@ __device__ __forceinline__ float4 pair_at(const float4* tab, uint32_t off) {
     return *reinterpret_cast<const float4*>(reinterpret_cast<const char*>(tab) + off);
 }
 
-// (ca, cb) of column q of a lane from its row's label word.
-// Code shapes that use the label-pair table (S polarisation).
+// Code shapes with the paired FP32 lean path (5 and 6, at most 16 labels);
+// for S polarisation their coefficients come from the label-pair table.
 template <int V>
 constexpr bool kPairShape = (V == 5 || V == 6);
 
+// S: (ca, cb) of column q of a lane from its row's label word.
 template <int V>
 __device__ __forceinline__ float2 coef_s(const Lane& ln, uint32_t w, int q) {
     if (kPairShape<V>) {
@@ -163,10 +164,19 @@ __device__ __forceinline__ void advance_lean_pair(Pipe<K>& p, V4& fE, V4& fX,
         const float2 dhx23 = __ffma2_rn(p.X[k].b, M1, fX.b);
         const float2 dhy01 = f2(__fsub_rn(p.Y[k][1], p.Y[k][0]), __fsub_rn(p.Y[k][2], p.Y[k][1]));
         const float2 dhy23 = f2(__fsub_rn(p.Y[k][3], p.Y[k][2]), __fsub_rn(yR, p.Y[k][3]));
-        const float2 e01 = __ffma2_rn(f2(c01.z, c01.w), __fadd2_rn(dhy01, dhx01),
-                                      __fmul2_rn(f2(c01.x, c01.y), p.E[k].a));
-        const float2 e23 = __ffma2_rn(f2(c23.z, c23.w), __fadd2_rn(dhy23, dhx23),
-                                      __fmul2_rn(f2(c23.x, c23.y), p.E[k].b));
+        const float2 cu01 = __fadd2_rn(dhy01, dhx01);
+        const float2 cu23 = __fadd2_rn(dhy23, dhx23);
+        const float2 e01 = __ffma2_rn(f2(c01.z, c01.w), cu01, __fmul2_rn(f2(c01.x, c01.y), p.E[k].a));
+        const float2 e23 = __ffma2_rn(f2(c23.z, c23.w), cu23, __fmul2_rn(f2(c23.x, c23.y), p.E[k].b));
+        if (V == 6) {
+            // code shape 6: step n0+k's gradient factors of this row (adjoint tape)
+            const int r = t - k - 1;
+            if (ln.own && r >= ln.y0 && r < ln.y1) {
+                float* tp = a.tape[k] + (size_t)r * a.s.pitch + ln.gx;
+                st4(tp, p.E[k]);
+                *reinterpret_cast<float4*>(tp + a.tape_f) = make_float4(cu01.x, cu01.y, cu23.x, cu23.y);
+            }
+        }
         const float2 d01 = __ffma2_rn(p.E[k + 1].a, M1, e01);
         const float2 d23 = __ffma2_rn(p.E[k + 1].b, M1, e23);
         const float2 x01 = __ffma2_rn(S2, d01, p.X[k].a);
@@ -176,17 +186,6 @@ __device__ __forceinline__ void advance_lean_pair(Pipe<K>& p, V4& fE, V4& fX,
         const float2 dy23 = f2(__fsub_rn(e23.x, e01.y), __fsub_rn(e23.y, e23.x));
         const float2 y01 = __ffma2_rn(S2, dy01, p.Y[k].a);
         const float2 y23 = __ffma2_rn(S2, dy23, p.Y[k].b);
-        if (V == 6 && k + 1 < K) {
-            // code shape 6: the state after step k+1 of this row (adjoint tape)
-            const int r = t - k - 1;
-            if (ln.own && r >= ln.y0 && r < ln.y1) {
-                float* tp = a.tape[k] + (size_t)r * a.s.pitch + ln.gx;
-                *reinterpret_cast<float4*>(tp) = make_float4(e01.x, e01.y, e23.x, e23.y);
-                *reinterpret_cast<float4*>(tp + a.tape_f) = make_float4(x01.x, x01.y, x23.x, x23.y);
-                *reinterpret_cast<float4*>(tp + 2 * a.tape_f) =
-                    make_float4(y01.x, y01.y, y23.x, y23.y);
-            }
-        }
         // level k now waits at row r+1; the new level-(k+1) row r flows up
         p.E[k] = fE; p.X[k] = fX; p.Y[k] = fY;
         fE.a = e01; fE.b = e23;
@@ -270,6 +269,7 @@ __device__ __forceinline__ void advance(Pipe<K>& p, V4& fE, V4& fX,
     for (int k = 0; k < K; ++k) {
         const int r = t - k - 1;
         float oE[4], oX[4], oY[4];
+        float cu[4];   // code shapes 4, 6: the factor of cb in the Ez update (adjoint tape)
         const uint32_t cL = p.L[k];
         // P: packed label-pair indices (labels < 16) of the top and left edges
         uint32_t xP = 0u, yP = 0u;
@@ -313,6 +313,7 @@ __device__ __forceinline__ void advance(Pipe<K>& p, V4& fE, V4& fX,
                     float dhx = __fsub_rn(fX[q], p.X[k][q]);
                     if (tf) dhx = __fsub_rn(dhx, hinc);
                     psi[q] = psi_new(b, c, psi[q], dhx);
+                    if (V == 4 || V == 6) cu[q] = __fadd_rn(dhy, __fmaf_rn(dhx, ik, psi[q]));
                     oE[q] = ez_new_pml(cc.x, cc.y, p.E[k][q], dhy, dhx, ik, psi[q]);
                 }
                 if (k == K - 1) {
@@ -320,8 +321,6 @@ __device__ __forceinline__ void advance(Pipe<K>& p, V4& fE, V4& fX,
                         st4(a.psiE_out + (size_t)pe * a.s.pitch + ln.gx, psi);
                 } else {
                     ringE[(r % K) * 32] = make_float4(psi[0], psi[1], psi[2], psi[3]);
-                    if ((V == 4 || V == 6) && ln.own && r >= ln.y0 && r < ln.y1)
-                        st4(a.tape[k] + 3 * a.tape_f + (size_t)pe * a.s.pitch + ln.gx, psi);
                 }
             } else {
 #pragma unroll
@@ -330,6 +329,7 @@ __device__ __forceinline__ void advance(Pipe<K>& p, V4& fE, V4& fX,
                     const float dhy = __fsub_rn(q < 3 ? p.Y[k][q + 1] : yR, p.Y[k][q]);
                     float dhx = __fsub_rn(fX[q], p.X[k][q]);
                     if (tf) dhx = __fsub_rn(dhx, hinc);
+                    if (V == 4 || V == 6) cu[q] = __fadd_rn(dhy, dhx);
                     oE[q] = ez_new(cc.x, cc.y, p.E[k][q], dhy, dhx);
                 }
             }
@@ -394,13 +394,14 @@ __device__ __forceinline__ void advance(Pipe<K>& p, V4& fE, V4& fX,
                     oY[q] = h_new(p.Y[k][q], S, dy);
                 }
             }
-            if ((V == 4 || V == 6) && k + 1 < K && ln.own && r >= ln.y0 && r < ln.y1 &&
+            if ((V == 4 || V == 6) && ln.own && r >= ln.y0 && r < ln.y1 &&
                 index_ok(r >= 0 && r < ln.ny && ln.col_ok, kSiteTape, a.s.dbg)) {
-                // code shape 4: the state after step k+1 of this row
+                // code shapes 4, 6: step n0+k's gradient factors of this row
+                // (Ez before the update and the factor of cb)
                 float* t = a.tape[k] + (size_t)r * a.s.pitch + ln.gx;
-                st4(t, oE);
-                st4(t + a.tape_f, oX);
-                st4(t + 2 * a.tape_f, oY);
+                const float eo[4] = {p.E[k][0], p.E[k][1], p.E[k][2], p.E[k][3]};
+                st4(t, eo);
+                st4(t + a.tape_f, cu);
             }
             if (GENERAL && ln.own && index_ok(ln.col_ok, kSiteDft, a.s.dbg)) {
                 if (ln.own_r && r == a.s.jr) {
@@ -455,8 +456,10 @@ __device__ __forceinline__ void advance(Pipe<K>& p, V4& fE, V4& fX,
 // through a shared-memory ring filled kRing rows ahead by cp.async, two rows
 // per loop trip on lean stretches; 3 the ring with one row per trip (built
 // under a register cap, see k_blocked_cap); 4 the ring, one row per trip,
-// that also stores the state after every intermediate step of the launch
-// (its owned rows) into BlockedArgs::tape, for the adjoint's recompute;
+// that also stores, for each step n of the launch and each owned row, the
+// two factors of the adjoint's gradient sums, Ez^{n-1/2} and the factor of
+// cb in the Ez update (the curl with its CPML and TF/SF terms), into
+// BlockedArgs::tape, for the adjoint's recompute;
 // 5 (at most 16 labels) shape 2 with paired FP32 instructions on the lean
 // path: for S with the label-pair coefficient table (advance_lean_pair),
 // for P on the centre update and the edge differences along s

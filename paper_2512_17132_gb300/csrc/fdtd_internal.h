@@ -70,9 +70,9 @@ struct BlockedArgs {
     const int* seg_y0;
     int n_strips, n_tasks, w_int;
     int64_t n_base;               // batch launches: absolute step of the batch start
-    // code shape 4 (adjoint recompute): states after each of steps 1..K-1 of
-    // the launch, as base pointers of [Ez | Hx | Hy | psi_E] blocks of
-    // tape_f, tape_f, tape_f floats and 2P rows
+    // code shapes 4 and 6 (adjoint recompute): for each step n0+k of the
+    // launch (k = 0..K-1) the base pointer tape[k] of a [Ez^{n-1/2} | factor
+    // of cb in the Ez update] block of tape_f + tape_f floats (pitch layout)
     float* const* tape;
     size_t tape_f;
 };
@@ -101,8 +101,10 @@ struct TwinArgs {
 
 struct BlockPlan;
 // launchers (kernels.cu, blocked.cu)
+// tape (S only): the step's gradient factors for the adjoint (k_naive_e)
 void launch_naive_step(const StepArgs& a, float* ez, float* hx, float* hy,
-                       float* psiE, float* psiH, int64_t n, cudaStream_t st);
+                       float* psiE, float* psiH, int64_t n, cudaStream_t st,
+                       float* tape = nullptr, size_t tape_f = 0);
 void launch_twin(const TwinArgs& a, int64_t n0, int steps, cudaStream_t st);
 void launch_flux(const double2* dft, const double2* twin_dft, int nx, double* out,
                  cudaStream_t st);

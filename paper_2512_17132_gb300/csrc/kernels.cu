@@ -11,9 +11,13 @@ namespace fdtd {
 // Centre field n-1/2 -> n+1/2 on every cell: Ez (S, Sec. 2.3 TMz Ez update)
 // or F = eta0 Hz (P, TEz Hz update, loss-free coefficients (1, S)), with the
 // CPML recursion in the top/bottom rows and the TF/SF correction at js.
+// With a tape (S, the adjoint's recompute) it also stores the step's two
+// gradient factors of each cell: Ez^{n-1/2} at tape and the factor of cb in
+// the update (the curl with its CPML and TF/SF terms) at tape + tape_f.
 template <int POL>
 __global__ void k_naive_e(StepArgs a, float* __restrict__ ez, const float* __restrict__ hx,
-                          const float* __restrict__ hy, float* __restrict__ psiE, int64_t n) {
+                          const float* __restrict__ hy, float* __restrict__ psiE, int64_t n,
+                          float* __restrict__ tape, size_t tape_f) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
     if (i >= a.nx) return;
@@ -34,8 +38,16 @@ __global__ void k_naive_e(StepArgs a, float* __restrict__ ez, const float* __res
         const float p = psi_new(b, cc, *pp, dhx);
         *pp = p;
         ez[o] = ez_new_pml(c.x, c.y, e, dhy, dhx, ik, p);
+        if (tape) {
+            tape[o] = e;
+            tape[tape_f + o] = __fadd_rn(dhy, __fmaf_rn(dhx, ik, p));
+        }
     } else {
         ez[o] = ez_new(c.x, c.y, e, dhy, dhx);
+        if (tape) {
+            tape[o] = e;
+            tape[tape_f + o] = __fadd_rn(dhy, dhx);
+        }
     }
 }
 
@@ -92,14 +104,14 @@ __global__ void k_naive_dft(StepArgs a, const float* __restrict__ ez,
 }
 
 void launch_naive_step(const StepArgs& a, float* ez, float* hx, float* hy, float* psiE,
-                       float* psiH, int64_t n, cudaStream_t st) {
+                       float* psiH, int64_t n, cudaStream_t st, float* tape, size_t tape_f) {
     dim3 blk(256);
     dim3 grd((a.nx + 255) / 256, a.ny);
     if (a.pol == 0) {
-        k_naive_e<0><<<grd, blk, 0, st>>>(a, ez, hx, hy, psiE, n);
+        k_naive_e<0><<<grd, blk, 0, st>>>(a, ez, hx, hy, psiE, n, tape, tape_f);
         k_naive_h<0><<<grd, blk, 0, st>>>(a, ez, hx, hy, psiH, n);
     } else {
-        k_naive_e<1><<<grd, blk, 0, st>>>(a, ez, hx, hy, psiE, n);
+        k_naive_e<1><<<grd, blk, 0, st>>>(a, ez, hx, hy, psiE, n, nullptr, 0);
         k_naive_h<1><<<grd, blk, 0, st>>>(a, ez, hx, hy, psiH, n);
     }
     k_naive_dft<<<dim3((a.nx + 255) / 256, 2), blk, 0, st>>>(a, ez, hx, n);
