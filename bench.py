@@ -629,6 +629,8 @@ def run_c5(args):
     sim = fdtd.Simulation(spec)
     if args.adj_block >= 0:
         fdtd.fdtd_set_option(sim.h, fdtd.FDTD_OPT_ADJ_BLOCK, args.adj_block)
+    if args.plan_weight > 0:
+        fdtd.fdtd_set_option(sim.h, fdtd.FDTD_OPT_PLAN_WEIGHT, round(args.plan_weight * 1000))
     fdtd.fdtd_forward_checkpointed(sim.h, min(2000, spec.steps), 500)   # warm-up
     fdtd.fdtd_backward(sim.h, 1.0, 0.0, spec.ny, spec.nx, len(spec.materials))
     clocks = ClockSampler(_device_id())

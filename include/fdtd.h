@@ -144,8 +144,10 @@ typedef struct fdtd_stats {
                                   internal (EINVAL) */
 #define FDTD_OPT_GRAPH 7       /* batches: replay captured CUDA graphs of launch chunks (default 1) */
 #define FDTD_OPT_PLAN_WEIGHT 8 /* segment planner: cost of a general-path iteration of the blocked
-                                  kernel in lean iterations, times 1000 (0: the measured default,
-                                  12 for S and 7.5 for P); batches take each handle's value */
+                                  kernel in lean iterations, times 1000 (0: the measured defaults,
+                                  12 for S and 7.5 for P, and for fdtd_backward 8 for the
+                                  recompute and 9 for the reverse kernel); batches take each
+                                  handle's value */
 #define FDTD_OPT_ADJ_BLOCK 11    /* fdtd_backward: reverse steps per launch of the temporally
                                   blocked reverse kernel, 1..4 (default 3), or 0 for one launch
                                   pair per reverse step; labelled handles with nx % 4 == 0 (the

@@ -806,7 +806,8 @@ int adj_blocked_per_sm(int K) {
 
 // Segment plan of the blocked reverse kernel for depth K: the forward
 // planner's cuts (segment_bounds) for the segment count that minimises
-// waves x (rows + 2K) with this kernel's own occupancy.
+// waves x (rows + 2K) with this kernel's own occupancy and general-path
+// weight.
 struct AdjPlan {
     int K = 0, n_strips = 0, n_segs = 0, w_int = 0;
     int* d_seg = nullptr;
@@ -830,7 +831,8 @@ AdjPlan make_adj_plan(fdtd_handle* h, int K) {
         const double cost = (double)waves * (rows + 2.0 * K);
         if (cost < best - 1e-9) { best = cost; seg = (int)rows; }
     }
-    const std::vector<int> bnd = segment_bounds(h->g, std::max(seg, K + 1), K, 0, h->opt_weight);
+    const double wg = h->opt_weight > 0.0 ? h->opt_weight : kReverseGeneralCost;
+    const std::vector<int> bnd = segment_bounds(h->g, std::max(seg, K + 1), K, 0, wg);
     pl.n_segs = (int)bnd.size() - 1;
     ACK(cudaMalloc(&pl.d_seg, bnd.size() * sizeof(int)));
     ACK(cudaMemcpy(pl.d_seg, bnd.data(), bnd.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -902,9 +904,12 @@ void steps_to_tape(fdtd_handle* h, const StateView& in, const StateView& out, in
                    float* const* tape_ptrs, double2* dummy) {
     StepArgs s = step_args(h);
     s.dft = dummy;
+    // code shape 6 (label-pair table, paired lean path) where the labels fit
+    const int shape = pair_shape_ok(false, h->maps, h->n_labels) ? 6 : 4;
     const int keep = h->opt_seg;
     h->opt_seg = 0;
-    BlockPlan& pl = get_plan(h, K);
+    BlockPlan& pl = plan_for(h, h->tape_plans, K, shape,
+                             h->opt_weight > 0.0 ? h->opt_weight : kTapeGeneralCost);
     h->opt_seg = keep;
     BlockedArgs b{};
     b.s = s;
@@ -917,8 +922,6 @@ void steps_to_tape(fdtd_handle* h, const StateView& in, const StateView& out, in
     b.w_int = pl.w_int;
     b.tape = tape_ptrs;
     b.tape_f = (size_t)h->pitch * h->g.ny;
-    // code shape 6 (label-pair table, paired lean path) where the labels fit
-    const int shape = pair_shape_ok(false, h->maps, h->n_labels) ? 6 : 4;
     launch_blocked(b, K, shape, n, h->stream);
 }
 

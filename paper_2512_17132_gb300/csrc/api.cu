@@ -383,26 +383,29 @@ std::vector<int> segment_bounds(const fdtd_grid& g, int seg, int K, int pol, dou
 // task per (strip, segment); with W warps resident on the whole GPU, the
 // segment count is chosen to minimise waves x (rows per segment + 2K), the
 // cost model of a wave of equal tasks that each stream their rows plus
-// the K-row halos above and below.
-BlockPlan& get_plan(fdtd_handle* h, int K) {
-    if ((int)h->plans.size() <= K) h->plans.resize(K + 1);
-    BlockPlan& p = h->plans[K];
+// the K-row halos above and below. `cache` holds one plan per depth for
+// code shape `variant` and planner weight `weight` (0: the default of the
+// polarisation).
+BlockPlan& plan_for(fdtd_handle* h, std::vector<BlockPlan>& cache, int K, int variant,
+                    double weight) {
+    if ((int)cache.size() <= K) cache.resize(K + 1);
+    BlockPlan& p = cache[K];
     const int want_seg = h->opt_seg;
-    if (p.K == K && p.d_seg_y0 && p.variant == h->opt_variant && p.weight == h->opt_weight &&
+    if (p.K == K && p.d_seg_y0 && p.variant == variant && p.weight == weight &&
         (want_seg == 0 || want_seg == p.seg_rows))
         return p;
     dfree(p.d_seg_y0);
     const fdtd_grid& g = h->g;
     p.K = K;
-    p.variant = h->opt_variant;
-    p.weight = h->opt_weight;
+    p.variant = variant;
+    p.weight = weight;
     p.halo = (K + 3) / 4 * 4;
     p.w_int = 128 - 2 * p.halo;
     p.n_strips = (g.nx + p.w_int - 1) / p.w_int;
     const int min_seg = K + 1;
     int seg = want_seg;
     if (seg <= 0) {
-        int per_sm = blocked_warps_per_sm(K, h->opt_variant, h->src.polarization);
+        int per_sm = blocked_warps_per_sm(K, variant, h->src.polarization);
         if (per_sm <= 0) per_sm = 8;
         const int64_t W = (int64_t)sm_count(h) * per_sm;
         double best = 1e300;
@@ -420,12 +423,16 @@ BlockPlan& get_plan(fdtd_handle* h, int K) {
         }
     }
     seg = std::max(seg, min_seg);
-    const std::vector<int> b = segment_bounds(g, seg, K, h->src.polarization, h->opt_weight);
+    const std::vector<int> b = segment_bounds(g, seg, K, h->src.polarization, weight);
     p.n_segs = (int)b.size() - 1;
     p.seg_rows = seg;
     CK(cudaMalloc(&p.d_seg_y0, b.size() * sizeof(int)));
     CK(cudaMemcpy(p.d_seg_y0, b.data(), b.size() * sizeof(int), cudaMemcpyHostToDevice));
     return p;
+}
+
+BlockPlan& get_plan(fdtd_handle* h, int K) {
+    return plan_for(h, h->plans, K, h->opt_variant, h->opt_weight);
 }
 
 int choose_kernel(fdtd_handle* h) {
@@ -543,6 +550,7 @@ void free_all(fdtd_handle* h) {
     if (h->h_phH) cudaFreeHost(h->h_phH);
     h->h_flux = nullptr; h->h_hinc = nullptr; h->h_einc = nullptr; h->h_phE = nullptr; h->h_phH = nullptr;
     for (auto& p : h->plans) dfree(p.d_seg_y0);
+    for (auto& p : h->tape_plans) dfree(p.d_seg_y0);
     for (auto& pr : h->timing_events) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     for (auto& pr : h->event_pool) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     h->timing_events.clear(); h->event_pool.clear();

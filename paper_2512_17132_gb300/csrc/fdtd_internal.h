@@ -158,6 +158,17 @@ void sync_all(fdtd_handle* h);
 // measured default of the polarisation)
 std::vector<int> segment_bounds(const fdtd_grid& g, int seg, int K, int pol, double weight = 0.0);
 BlockPlan& get_plan(fdtd_handle* h, int K);
+BlockPlan& plan_for(fdtd_handle* h, std::vector<BlockPlan>& cache, int K, int variant,
+                    double weight);
+// Planner weights (lean iterations per general-path iteration) of the
+// adjoint's kernels (S) where the handle sets none, measured on config 5
+// (1000 x 6000, 30 000 steps; backward Gcell-updates/s for recompute /
+// reverse weights): 12/12: 131.5, 12/9: 136.2, 10/9: 139.0, 8/12: 134.9,
+// 8/9: 139.8, 8/6: 132.6, 6/9: 133.7, 8/4: 129.5. The recompute (code shapes
+// 4 and 6) stores the gradient factors of every row, which makes its lean
+// iterations dearer and the general path relatively cheaper.
+inline constexpr double kTapeGeneralCost = 8.0;
+inline constexpr double kReverseGeneralCost = 9.0;
 
 }  // namespace fdtd
 
@@ -214,8 +225,9 @@ struct fdtd_handle {
     double2* h_phE = nullptr; double2* h_phH = nullptr;    // pinned
     int64_t tab_uploaded = 0;   // table entries [0, tab_uploaded) are on the device
     cudaEvent_t ev_tab = nullptr, ev_twin = nullptr;
-    // blocked-kernel plans per depth
+    // blocked-kernel plans per depth: the forward's and the adjoint recompute's
     std::vector<fdtd::BlockPlan> plans;
+    std::vector<fdtd::BlockPlan> tape_plans;
     // options
     int opt_kernel = 0, opt_block = 8, opt_seg = 0, opt_timing = 0, opt_variant = 2;
     double opt_weight = 0.0;    // planner weight of a general-path iteration (0: default)
