@@ -149,13 +149,12 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 // subtraction, so the results are bit for bit those of advance(). The
 // differences along x take a column pair shifted by one and stay scalar.
 template <int K, int V>
-__device__ __forceinline__ void advance_lean_pair(Pipe<K>& p, V4& fE, V4& fX,
-                                                  V4& fY, uint32_t& fL, const Lane& ln,
-                                                  const BlockedArgs& a, const int t) {
+__device__ __forceinline__ void lean_pair_level(Pipe<K>& p, const int k, V4& fE, V4& fX,
+                                                V4& fY, uint32_t& fL, const Lane& ln,
+                                                const BlockedArgs& a, const int t) {
     const float2 S2 = f2(ln.S, ln.S);
     const float2 M1 = f2(-1.0f, -1.0f);
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
+    {
         const uint32_t cL = p.L[k];
         const float4 c01 = pair_at(ln.pair, cL & 0xffffu);
         const float4 c23 = pair_at(ln.pair, cL >> 16);
@@ -193,6 +192,36 @@ __device__ __forceinline__ void advance_lean_pair(Pipe<K>& p, V4& fE, V4& fX,
         fY.a = y01; fY.b = y23;
         p.L[k] = fL;
         fL = cL;
+    }
+}
+
+template <int K, int V>
+__device__ __forceinline__ void advance_lean_pair(Pipe<K>& p, V4& fE, V4& fX,
+                                                  V4& fY, uint32_t& fL, const Lane& ln,
+                                                  const BlockedArgs& a, const int t) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) lean_pair_level<K, V>(p, k, fE, fX, fY, fL, ln, a, t);
+}
+
+// Two lean S rows t and t+1 of code shape 5 in one pass over the levels,
+// row t+1 one level behind row t: level k of row t+1 needs level k of row t
+// (its pending rows) and level k-1 of row t+1, so at stage s the code
+// holds level s of row t and level s-1 of row t+1, two independent chains.
+// Row t leaves the pipeline (finish0: its level-K row stored, level K's
+// pending row set) before row t+1's last level reads it. The same
+// per-level expressions in an order that keeps every dependency, so the
+// same bits.
+template <int K, typename F>
+__device__ __forceinline__ void advance_lean_pair2(Pipe<K>& p, V4& fE0, V4& fX0, V4& fY0,
+                                                   uint32_t& fL0, V4& fE1, V4& fX1, V4& fY1,
+                                                   uint32_t& fL1, const Lane& ln,
+                                                   const BlockedArgs& a, const int t,
+                                                   F&& finish0) {
+#pragma unroll
+    for (int s = 0; s <= K; ++s) {
+        if (s < K) lean_pair_level<K, 5>(p, s, fE0, fX0, fY0, fL0, ln, a, t);
+        if (s == K) finish0();
+        if (s >= 1) lean_pair_level<K, 5>(p, s - 1, fE1, fX1, fY1, fL1, ln, a, t + 1);
     }
 }
 
@@ -465,7 +494,10 @@ __device__ __forceinline__ void advance(Pipe<K>& p, V4& fE, V4& fX,
 // for P on the centre update and the edge differences along s
 // (advance_lean_pair_p); 6 (S, at most 16 labels) shape 4 with the
 // label-pair table and the paired lean path (the adjoint's recompute).
-template <int K, int V, int POL>
+// SKEW (S, shape 5): the two lean rows of a loop trip run skewed by one
+// level (advance_lean_pair2), which exposes two independent dependency
+// chains; the batched kernel leaves it off (its extra registers spill there).
+template <int K, int V, int POL, bool SKEW = true>
 __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float4* s_tab,
                                              const int task, const int64_t n0) {
     constexpr int H = ((K + 3) / 4) * 4;
@@ -558,6 +590,35 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float4*
 #pragma unroll
         for (int d = 0; d < kRing; ++d) issue(t_begin + d, d);
         int slot = 0;
+        // level-0 row of ring slot `sl` as pipeline input (S, code shape 5)
+        auto take = [&](const int sl, V4& fE, V4& fX, V4& fY, uint32_t& fL) {
+            const float4 e4 = ring[sl][0][lane], x4 = ring[sl][1][lane], y4 = ring[sl][2][lane];
+            fL = ring_l[sl][lane];
+            index_ok(((fL & 0xffu) < (unsigned)a.s.n_labels) &&
+                         (((fL >> 8) & 0xffu) < (unsigned)a.s.n_labels) &&
+                         (((fL >> 16) & 0xffu) < (unsigned)a.s.n_labels) &&
+                         ((fL >> 24) < (unsigned)a.s.n_labels),
+                     kSiteLabel, a.s.dbg);
+            fL = pair_offsets(fL);
+            fE.a = make_float2(e4.x, e4.y); fE.b = make_float2(e4.z, e4.w);
+            fX.a = make_float2(x4.x, x4.y); fX.b = make_float2(x4.z, x4.w);
+            fY.a = make_float2(y4.x, y4.y); fY.b = make_float2(y4.z, y4.w);
+        };
+        // two lean rows t, t+1 (S, code shape 5), skewed by one level
+        auto row2 = [&](const int t) {
+            cp_async_wait<kRing - 2>();
+            V4 fE0, fX0, fY0, fE1, fX1, fY1;
+            uint32_t fL0, fL1;
+            const int s1 = (slot + 1 == kRing) ? 0 : slot + 1;
+            take(slot, fE0, fX0, fY0, fL0);
+            take(s1, fE1, fX1, fY1, fL1);
+            issue(t + kRing, slot);
+            issue(t + 1 + kRing, s1);
+            slot = (s1 + 1 == kRing) ? 0 : s1 + 1;
+            advance_lean_pair2<K>(p, fE0, fX0, fY0, fL0, fE1, fX1, fY1, fL1, ln, a, t,
+                                  [&]() { finish(t, fE0, fX0, fY0); });
+            finish(t + 1, fE1, fX1, fY1);
+        };
         auto row = [&](const int t, const bool fast) {
             cp_async_wait<kRing - 1>();
             V4 fE, fX, fY;
@@ -595,7 +656,10 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float4*
         // rows the two register sets alternate and the copies disappear.
 #pragma unroll 1
         for (int t = t_begin; t < t_end;) {
-            if ((V == 2 || V == 5) && t + 1 < t_end && is_fast(t) && is_fast(t + 1)) {
+            if (SKEW && V == 5 && POL == 0 && t + 1 < t_end && is_fast(t) && is_fast(t + 1)) {
+                row2(t);
+                t += 2;
+            } else if ((V == 2 || V == 5) && t + 1 < t_end && is_fast(t) && is_fast(t + 1)) {
                 row(t, true);
                 row(t + 1, true);
                 t += 2;
@@ -715,7 +779,7 @@ __device__ __forceinline__ void blocked_batch_body(const BatchArgs& b, const int
     const BlockedArgs& a = *reinterpret_cast<const BlockedArgs*>(s_raw);
     load_coef_table<V, POL>(a.s, s_tab);
     const int64_t n0 = a.n_base + *b.step_base + step_off;
-    blocked_task<K, V, POL>(a, s_tab, task - b.first_task[sim], n0);
+    blocked_task<K, V, POL, false>(a, s_tab, task - b.first_task[sim], n0);
 }
 
 // Many independent simulations in one launch: the grid covers the union of
