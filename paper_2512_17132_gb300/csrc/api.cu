@@ -283,9 +283,11 @@ int sm_count(fdtd_handle* h) {
 // lookups of the edge coefficients), so its ratio is lower. Measured on
 // GB300 on config 2 (Gcell-updates/s, 8192 steps per run): S with code
 // shape 5 (the S default): 9: 1350, 10: 1462, 11: 1521, 12: 1543, 13: 1385,
-// 15: 1268; P 7.5: 967, 11: 899. Away from the best weight the cuts shift
-// whole general-path rows between tasks, so the response is uneven.
-constexpr double kGeneralCost[2] = {12.0, 7.5};
+// 15: 1268, and with the skewed two-row trip 11: 1539, 12: 1604, 13: 1407;
+// P with code shape 5 and the skewed trip 6.5: 1152, 7.5: 1281, 8.5: 1318,
+// 9: 1239. Away from the best weight the cuts shift whole general-path rows
+// between tasks, so the response is uneven.
+constexpr double kGeneralCost[2] = {12.0, 8.5};
 
 double general_cost(int pol, double override_w) {
     return override_w > 0.0 ? override_w : kGeneralCost[pol ? 1 : 0];

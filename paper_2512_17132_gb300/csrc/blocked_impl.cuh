@@ -203,41 +203,18 @@ __device__ __forceinline__ void advance_lean_pair(Pipe<K>& p, V4& fE, V4& fX,
     for (int k = 0; k < K; ++k) lean_pair_level<K, V>(p, k, fE, fX, fY, fL, ln, a, t);
 }
 
-// Two lean S rows t and t+1 of code shape 5 in one pass over the levels,
-// row t+1 one level behind row t: level k of row t+1 needs level k of row t
-// (its pending rows) and level k-1 of row t+1, so at stage s the code
-// holds level s of row t and level s-1 of row t+1, two independent chains.
-// Row t leaves the pipeline (finish0: its level-K row stored, level K's
-// pending row set) before row t+1's last level reads it. The same
-// per-level expressions in an order that keeps every dependency, so the
-// same bits.
-template <int K, typename F>
-__device__ __forceinline__ void advance_lean_pair2(Pipe<K>& p, V4& fE0, V4& fX0, V4& fY0,
-                                                   uint32_t& fL0, V4& fE1, V4& fX1, V4& fY1,
-                                                   uint32_t& fL1, const Lane& ln,
-                                                   const BlockedArgs& a, const int t,
-                                                   F&& finish0) {
-#pragma unroll
-    for (int s = 0; s <= K; ++s) {
-        if (s < K) lean_pair_level<K, 5>(p, s, fE0, fX0, fY0, fL0, ln, a, t);
-        if (s == K) finish0();
-        if (s >= 1) lean_pair_level<K, 5>(p, s - 1, fE1, fX1, fY1, fL1, ln, a, t + 1);
-    }
-}
-
 // Lean P iteration of code shape 5: the same pipeline as advance() for
 // POL = 1 with the loss-free centre update and the two edge differences
 // along s paired (f32x2); the centre's coefficient 1 is dropped (1 * F is F
 // exactly) and the lossy edge updates keep their per-edge label-pair
 // coefficients (scalar). Bit for bit the results of advance().
 template <int K>
-__device__ __forceinline__ void advance_lean_pair_p(Pipe<K>& p, V4& fE, V4& fX,
-                                                    V4& fY, uint32_t& fL, uint32_t& fLY,
-                                                    const Lane& ln) {
+__device__ __forceinline__ void lean_pair_p_level(Pipe<K>& p, const int k, V4& fE, V4& fX,
+                                                  V4& fY, uint32_t& fL, uint32_t& fLY,
+                                                  const Lane& ln) {
     const float2 S2 = f2(ln.S, ln.S);
     const float2 M1 = f2(-1.0f, -1.0f);
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
+    {
         // the row's edge label pairs, formed once when the row was loaded
         const uint32_t xP = p.L[k], yP = p.LY[k];
         const float yR = __shfl_down_sync(FULL, p.Y[k][0], 1);
@@ -273,6 +250,45 @@ __device__ __forceinline__ void advance_lean_pair_p(Pipe<K>& p, V4& fE, V4& fX,
         fL = xP;
         p.LY[k] = fLY;
         fLY = yP;
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void advance_lean_pair_p(Pipe<K>& p, V4& fE, V4& fX,
+                                                    V4& fY, uint32_t& fL, uint32_t& fLY,
+                                                    const Lane& ln) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) lean_pair_p_level<K>(p, k, fE, fX, fY, fL, fLY, ln);
+}
+
+// Two lean rows t and t+1 of code shape 5 in one pass over the levels,
+// row t+1 one level behind row t: level k of row t+1 needs level k of row t
+// (its pending rows) and level k-1 of row t+1, so at stage s the code
+// holds level s of row t and level s-1 of row t+1, two independent chains.
+// Row t leaves the pipeline (finish0: its level-K row stored, level K's
+// pending row set) before row t+1's last level reads it. The same
+// per-level expressions in an order that keeps every dependency, so the
+// same bits.
+template <int K, int POL>
+__device__ __forceinline__ void lean_level5(Pipe<K>& p, const int k, V4& fE, V4& fX, V4& fY,
+                                            uint32_t& fL, uint32_t& fLY, const Lane& ln,
+                                            const BlockedArgs& a, const int t) {
+    if constexpr (POL == 0) lean_pair_level<K, 5>(p, k, fE, fX, fY, fL, ln, a, t);
+    else lean_pair_p_level<K>(p, k, fE, fX, fY, fL, fLY, ln);
+}
+
+template <int K, int POL, typename F>
+__device__ __forceinline__ void advance_lean_pair2(Pipe<K>& p, V4& fE0, V4& fX0, V4& fY0,
+                                                   uint32_t& fL0, uint32_t& fLY0, V4& fE1,
+                                                   V4& fX1, V4& fY1, uint32_t& fL1,
+                                                   uint32_t& fLY1, const Lane& ln,
+                                                   const BlockedArgs& a, const int t,
+                                                   F&& finish0) {
+#pragma unroll
+    for (int s = 0; s <= K; ++s) {
+        if (s < K) lean_level5<K, POL>(p, s, fE0, fX0, fY0, fL0, fLY0, ln, a, t);
+        if (s == K) finish0();
+        if (s >= 1) lean_level5<K, POL>(p, s - 1, fE1, fX1, fY1, fL1, fLY1, ln, a, t + 1);
     }
 }
 
@@ -590,40 +606,10 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float4*
 #pragma unroll
         for (int d = 0; d < kRing; ++d) issue(t_begin + d, d);
         int slot = 0;
-        // level-0 row of ring slot `sl` as pipeline input (S, code shape 5)
-        auto take = [&](const int sl, V4& fE, V4& fX, V4& fY, uint32_t& fL) {
+        // the level-0 row of ring slot `sl` as pipeline input
+        auto take = [&](const int sl, V4& fE, V4& fX, V4& fY, uint32_t& fL, uint32_t& fLY) {
             const float4 e4 = ring[sl][0][lane], x4 = ring[sl][1][lane], y4 = ring[sl][2][lane];
             fL = ring_l[sl][lane];
-            index_ok(((fL & 0xffu) < (unsigned)a.s.n_labels) &&
-                         (((fL >> 8) & 0xffu) < (unsigned)a.s.n_labels) &&
-                         (((fL >> 16) & 0xffu) < (unsigned)a.s.n_labels) &&
-                         ((fL >> 24) < (unsigned)a.s.n_labels),
-                     kSiteLabel, a.s.dbg);
-            fL = pair_offsets(fL);
-            fE.a = make_float2(e4.x, e4.y); fE.b = make_float2(e4.z, e4.w);
-            fX.a = make_float2(x4.x, x4.y); fX.b = make_float2(x4.z, x4.w);
-            fY.a = make_float2(y4.x, y4.y); fY.b = make_float2(y4.z, y4.w);
-        };
-        // two lean rows t, t+1 (S, code shape 5), skewed by one level
-        auto row2 = [&](const int t) {
-            cp_async_wait<kRing - 2>();
-            V4 fE0, fX0, fY0, fE1, fX1, fY1;
-            uint32_t fL0, fL1;
-            const int s1 = (slot + 1 == kRing) ? 0 : slot + 1;
-            take(slot, fE0, fX0, fY0, fL0);
-            take(s1, fE1, fX1, fY1, fL1);
-            issue(t + kRing, slot);
-            issue(t + 1 + kRing, s1);
-            slot = (s1 + 1 == kRing) ? 0 : s1 + 1;
-            advance_lean_pair2<K>(p, fE0, fX0, fY0, fL0, fE1, fX1, fY1, fL1, ln, a, t,
-                                  [&]() { finish(t, fE0, fX0, fY0); });
-            finish(t + 1, fE1, fX1, fY1);
-        };
-        auto row = [&](const int t, const bool fast) {
-            cp_async_wait<kRing - 1>();
-            V4 fE, fX, fY;
-            const float4 e4 = ring[slot][0][lane], x4 = ring[slot][1][lane], y4 = ring[slot][2][lane];
-            uint32_t fL = ring_l[slot][lane];
             // every label must index the coefficient table (debug builds)
             index_ok(((fL & 0xffu) < (unsigned)a.s.n_labels) &&
                          (((fL >> 8) & 0xffu) < (unsigned)a.s.n_labels) &&
@@ -633,7 +619,7 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float4*
             if (kPairShape<V> && POL == 0) fL = pair_offsets(fL);
             // P, code shape 5: the row's edge label pairs, formed once here
             // (top edges pair rows t-1 and t, left edges columns q-1 and q)
-            uint32_t fLY = 0u;
+            fLY = 0u;
             if (kPairShape<V> && POL == 1) {
                 const uint32_t raw = fL;
                 const uint32_t lNb = __shfl_up_sync(FULL, raw, 1) >> 24;   // column q-1 of lane 0
@@ -641,9 +627,30 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float4*
                 fL = (prevL << 4) | raw;
                 prevL = raw;
             }
-            fE[0] = e4.x; fE[1] = e4.y; fE[2] = e4.z; fE[3] = e4.w;
-            fX[0] = x4.x; fX[1] = x4.y; fX[2] = x4.z; fX[3] = x4.w;
-            fY[0] = y4.x; fY[1] = y4.y; fY[2] = y4.z; fY[3] = y4.w;
+            fE.a = make_float2(e4.x, e4.y); fE.b = make_float2(e4.z, e4.w);
+            fX.a = make_float2(x4.x, x4.y); fX.b = make_float2(x4.z, x4.w);
+            fY.a = make_float2(y4.x, y4.y); fY.b = make_float2(y4.z, y4.w);
+        };
+        // two lean rows t, t+1 (code shape 5), skewed by one level
+        auto row2 = [&](const int t) {
+            cp_async_wait<kRing - 2>();
+            V4 fE0, fX0, fY0, fE1, fX1, fY1;
+            uint32_t fL0, fLY0, fL1, fLY1;
+            const int s1 = (slot + 1 == kRing) ? 0 : slot + 1;
+            take(slot, fE0, fX0, fY0, fL0, fLY0);
+            take(s1, fE1, fX1, fY1, fL1, fLY1);
+            issue(t + kRing, slot);
+            issue(t + 1 + kRing, s1);
+            slot = (s1 + 1 == kRing) ? 0 : s1 + 1;
+            advance_lean_pair2<K, POL>(p, fE0, fX0, fY0, fL0, fLY0, fE1, fX1, fY1, fL1, fLY1,
+                                       ln, a, t, [&]() { finish(t, fE0, fX0, fY0); });
+            finish(t + 1, fE1, fX1, fY1);
+        };
+        auto row = [&](const int t, const bool fast) {
+            cp_async_wait<kRing - 1>();
+            V4 fE, fX, fY;
+            uint32_t fL, fLY;
+            take(slot, fE, fX, fY, fL, fLY);
             issue(t + kRing, slot);
             slot = (slot + 1 == kRing) ? 0 : slot + 1;
             if (fast) advance<K, false, POL, V>(p, fE, fX, fY, fL, fLY, t, a, ln, ringE, ringH, n0);
@@ -656,7 +663,7 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float4*
         // rows the two register sets alternate and the copies disappear.
 #pragma unroll 1
         for (int t = t_begin; t < t_end;) {
-            if (SKEW && V == 5 && POL == 0 && t + 1 < t_end && is_fast(t) && is_fast(t + 1)) {
+            if (SKEW && V == 5 && t + 1 < t_end && is_fast(t) && is_fast(t + 1)) {
                 row2(t);
                 t += 2;
             } else if ((V == 2 || V == 5) && t + 1 < t_end && is_fast(t) && is_fast(t + 1)) {
