@@ -269,15 +269,15 @@ __device__ __forceinline__ void advance_lean_pair_p(Pipe<K>& p, V4& fE, V4& fX,
 // pending row set) before row t+1's last level reads it. The same
 // per-level expressions in an order that keeps every dependency, so the
 // same bits.
-template <int K, int POL>
+template <int K, int V, int POL>
 __device__ __forceinline__ void lean_level5(Pipe<K>& p, const int k, V4& fE, V4& fX, V4& fY,
                                             uint32_t& fL, uint32_t& fLY, const Lane& ln,
                                             const BlockedArgs& a, const int t) {
-    if constexpr (POL == 0) lean_pair_level<K, 5>(p, k, fE, fX, fY, fL, ln, a, t);
+    if constexpr (POL == 0) lean_pair_level<K, V>(p, k, fE, fX, fY, fL, ln, a, t);
     else lean_pair_p_level<K>(p, k, fE, fX, fY, fL, fLY, ln);
 }
 
-template <int K, int POL, typename F>
+template <int K, int V, int POL, typename F>
 __device__ __forceinline__ void advance_lean_pair2(Pipe<K>& p, V4& fE0, V4& fX0, V4& fY0,
                                                    uint32_t& fL0, uint32_t& fLY0, V4& fE1,
                                                    V4& fX1, V4& fY1, uint32_t& fL1,
@@ -286,9 +286,9 @@ __device__ __forceinline__ void advance_lean_pair2(Pipe<K>& p, V4& fE0, V4& fX0,
                                                    F&& finish0) {
 #pragma unroll
     for (int s = 0; s <= K; ++s) {
-        if (s < K) lean_level5<K, POL>(p, s, fE0, fX0, fY0, fL0, fLY0, ln, a, t);
+        if (s < K) lean_level5<K, V, POL>(p, s, fE0, fX0, fY0, fL0, fLY0, ln, a, t);
         if (s == K) finish0();
-        if (s >= 1) lean_level5<K, POL>(p, s - 1, fE1, fX1, fY1, fL1, fLY1, ln, a, t + 1);
+        if (s >= 1) lean_level5<K, V, POL>(p, s - 1, fE1, fX1, fY1, fL1, fLY1, ln, a, t + 1);
     }
 }
 
@@ -509,10 +509,11 @@ __device__ __forceinline__ void advance(Pipe<K>& p, V4& fE, V4& fX,
 // path: for S with the label-pair coefficient table (advance_lean_pair),
 // for P on the centre update and the edge differences along s
 // (advance_lean_pair_p); 6 (S, at most 16 labels) shape 4 with the
-// label-pair table and the paired lean path (the adjoint's recompute).
-// SKEW (S, shape 5): the two lean rows of a loop trip run skewed by one
-// level (advance_lean_pair2), which exposes two independent dependency
-// chains; the batched kernel leaves it off (its extra registers spill there).
+// label-pair table, the paired lean path and two lean rows per trip (the
+// adjoint's recompute). SKEW (shapes 5 and 6): the two lean rows of a loop
+// trip run skewed by one level (advance_lean_pair2), which exposes two
+// independent dependency chains; the batched kernel leaves it off (its
+// extra registers spill there).
 template <int K, int V, int POL, bool SKEW = true>
 __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float4* s_tab,
                                              const int task, const int64_t n0) {
@@ -642,7 +643,7 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float4*
             issue(t + kRing, slot);
             issue(t + 1 + kRing, s1);
             slot = (s1 + 1 == kRing) ? 0 : s1 + 1;
-            advance_lean_pair2<K, POL>(p, fE0, fX0, fY0, fL0, fLY0, fE1, fX1, fY1, fL1, fLY1,
+            advance_lean_pair2<K, V, POL>(p, fE0, fX0, fY0, fL0, fLY0, fE1, fX1, fY1, fL1, fLY1,
                                        ln, a, t, [&]() { finish(t, fE0, fX0, fY0); });
             finish(t + 1, fE1, fX1, fY1);
         };
@@ -663,7 +664,7 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float4*
         // rows the two register sets alternate and the copies disappear.
 #pragma unroll 1
         for (int t = t_begin; t < t_end;) {
-            if (SKEW && V == 5 && t + 1 < t_end && is_fast(t) && is_fast(t + 1)) {
+            if (SKEW && kPairShape<V> && t + 1 < t_end && is_fast(t) && is_fast(t + 1)) {
                 row2(t);
                 t += 2;
             } else if ((V == 2 || V == 5) && t + 1 < t_end && is_fast(t) && is_fast(t + 1)) {
