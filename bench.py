@@ -369,9 +369,10 @@ def roofline_record(achieved, peak, peak_kind, algo_bytes, avg_launch_s, traffic
                 "issue peak = SMs x 4 schedulers x 1 warp instruction per clock x sampled SM clock"}
 
 
-def golden_rt_check(results, steps):
+def golden_rt_check(results, steps, pol):
     """R and T of the timed runs against the FP64 oracle's values for the
-    same full-length config-2 runs (tests/golden), where they exist."""
+    same full-length config-2 runs (tests/golden), where they exist: same
+    step count and the same polarisation ("s" or "p")."""
     errs = []
     for lam, (R, T) in results:
         path = os.path.join(ROOT, "tests", "golden", f"oracle_c2_{lam * 1e9:g}nm.json")
@@ -380,7 +381,8 @@ def golden_rt_check(results, steps):
                 g = json.load(f)
         except Exception:
             continue
-        if g.get("steps") != steps or g.get("R") is None:
+        if (g.get("steps") != steps or g.get("R") is None
+                or not str(g.get("polarization", "")).lower().startswith(pol)):
             continue
         errs.append((lam, abs(R - g["R"]), abs(T - g["T"])))
     if not errs:
@@ -761,7 +763,7 @@ def main():
         counters = measured_counters(spec0, steps_per_launch, st["variant"], p_sha)
     traffic = counters["dram_bytes_per_launch"] if counters else None
     inst = counters.get("warp_inst_per_launch") if counters else None
-    rt_check = golden_rt_check([(lam, rt) for lam, rt in results[W:]], spec0.steps)
+    rt_check = golden_rt_check([(lam, rt) for lam, rt in results[W:]], spec0.steps, args.pol)
     for s in sims.values():
         s.close()
 

@@ -58,15 +58,19 @@ def test_measured_counters_follow_kernel_shape_and_plan(monkeypatch, tmp_path):
 def test_golden_rt_check_compares_matching_runs(monkeypatch, tmp_path):
     g = tmp_path / "tests" / "golden"
     g.mkdir(parents=True)
-    (g / "oracle_c2_550nm.json").write_text(json.dumps({"steps": 30000, "R": 0.1, "T": 0.5}))
-    (g / "oracle_c2_800nm.json").write_text(json.dumps({"steps": 4000, "R": 0.2, "T": 0.4}))
+    (g / "oracle_c2_550nm.json").write_text(
+        json.dumps({"steps": 30000, "R": 0.1, "T": 0.5, "polarization": "S (TMz)"}))
+    (g / "oracle_c2_800nm.json").write_text(
+        json.dumps({"steps": 4000, "R": 0.2, "T": 0.4, "polarization": "S (TMz)"}))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     res = [(550e-9, (0.1004, 0.4999)), (800e-9, (0.3, 0.3)), (450e-9, (0.0, 0.0))]
-    d = bench.golden_rt_check(res, 30000)
+    d = bench.golden_rt_check(res, 30000, "s")
     # only the 550 nm run has a stored oracle run of the same length
     assert d["runs_checked"] == 1 and d["wavelengths_nm"] == [550]
     assert abs(d["max_abs_err_R"] - 4e-4) < 1e-12 and abs(d["max_abs_err_T"] - 1e-4) < 1e-12
-    assert bench.golden_rt_check(res, 1000) is None
+    assert bench.golden_rt_check(res, 1000, "s") is None
+    # the stored runs are S-polarised: a P line has nothing to compare with
+    assert bench.golden_rt_check(res, 30000, "p") is None
 
 
 def test_issue_fraction_of_the_roofline_record(monkeypatch):
