@@ -510,11 +510,10 @@ __device__ __forceinline__ void advance(Pipe<K>& p, V4& fE, V4& fX,
 // for P on the centre update and the edge differences along s
 // (advance_lean_pair_p); 6 (S, at most 16 labels) shape 4 with the
 // label-pair table, the paired lean path and two lean rows per trip (the
-// adjoint's recompute). SKEW (shapes 5 and 6): the two lean rows of a loop
-// trip run skewed by one level (advance_lean_pair2), which exposes two
-// independent dependency chains; the batched kernel leaves it off (its
-// extra registers spill there).
-template <int K, int V, int POL, bool SKEW = true>
+// adjoint's recompute). In shapes 5 and 6 the two lean rows of a loop trip
+// run skewed by one level (advance_lean_pair2), which exposes two
+// independent dependency chains.
+template <int K, int V, int POL>
 __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float4* s_tab,
                                              const int task, const int64_t n0) {
     constexpr int H = ((K + 3) / 4) * 4;
@@ -664,7 +663,7 @@ __device__ __forceinline__ void blocked_task(const BlockedArgs& a, const float4*
         // rows the two register sets alternate and the copies disappear.
 #pragma unroll 1
         for (int t = t_begin; t < t_end;) {
-            if (SKEW && kPairShape<V> && t + 1 < t_end && is_fast(t) && is_fast(t + 1)) {
+            if (kPairShape<V> && t + 1 < t_end && is_fast(t) && is_fast(t + 1)) {
                 row2(t);
                 t += 2;
             } else if ((V == 2 || V == 5) && t + 1 < t_end && is_fast(t) && is_fast(t + 1)) {
@@ -787,7 +786,7 @@ __device__ __forceinline__ void blocked_batch_body(const BatchArgs& b, const int
     const BlockedArgs& a = *reinterpret_cast<const BlockedArgs*>(s_raw);
     load_coef_table<V, POL>(a.s, s_tab);
     const int64_t n0 = a.n_base + *b.step_base + step_off;
-    blocked_task<K, V, POL, false>(a, s_tab, task - b.first_task[sim], n0);
+    blocked_task<K, V, POL>(a, s_tab, task - b.first_task[sim], n0);
 }
 
 // Many independent simulations in one launch: the grid covers the union of
