@@ -146,7 +146,7 @@ typedef struct fdtd_stats {
 #define FDTD_OPT_PLAN_WEIGHT 8 /* segment planner: cost of a general-path iteration of the blocked
                                   kernel in lean iterations, times 1000 (0: the measured defaults,
                                   12 for S and 8.5 for P, and for fdtd_backward 8 for the
-                                  recompute and 9 for the reverse kernel); batches take each
+                                  recompute and 10 for the reverse kernel); batches take each
                                   handle's value */
 #define FDTD_OPT_ADJ_BLOCK 11    /* fdtd_backward: reverse steps per launch of the temporally
                                   blocked reverse kernel, 1..4 (default 3), or 0 for one launch

@@ -163,12 +163,14 @@ BlockPlan& plan_for(fdtd_handle* h, std::vector<BlockPlan>& cache, int K, int va
 // Planner weights (lean iterations per general-path iteration) of the
 // adjoint's kernels (S) where the handle sets none, measured on config 5
 // (1000 x 6000, 30 000 steps; backward Gcell-updates/s for recompute /
-// reverse weights): 12/12: 131.5, 12/9: 136.2, 10/9: 139.0, 8/12: 134.9,
-// 8/9: 139.8, 8/6: 132.6, 6/9: 133.7, 8/4: 129.5. The recompute (code shapes
-// 4 and 6) stores the gradient factors of every row, which makes its lean
-// iterations dearer and the general path relatively cheaper.
+// reverse weights, with the recompute's skewed two-row trip): 6/8: 133.6,
+// 6/10: 133.7, 8/8: 141.8, 8/9: 139.8, 8/10: 141.9, 10/8: 138.9, 10/10:
+// 139.1, 12/8: 134.5, 12/10: 134.6; before that trip 12/12 gave 131.5 and
+// 8/12 134.9. The recompute (code shapes 4 and 6) stores the gradient
+// factors of every row, which makes its lean iterations dearer and the
+// general path relatively cheaper.
 inline constexpr double kTapeGeneralCost = 8.0;
-inline constexpr double kReverseGeneralCost = 9.0;
+inline constexpr double kReverseGeneralCost = 10.0;
 
 }  // namespace fdtd
 
