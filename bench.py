@@ -375,7 +375,8 @@ def golden_rt_check(results, steps, pol):
     step count and the same polarisation ("s" or "p")."""
     errs = []
     for lam, (R, T) in results:
-        path = os.path.join(ROOT, "tests", "golden", f"oracle_c2_{lam * 1e9:g}nm.json")
+        stem = "oracle_c2p" if pol == "p" else "oracle_c2"
+        path = os.path.join(ROOT, "tests", "golden", f"{stem}_{lam * 1e9:g}nm.json")
         try:
             with open(path) as f:
                 g = json.load(f)
@@ -390,7 +391,8 @@ def golden_rt_check(results, steps, pol):
     return {"max_abs_err_R": max(e[1] for e in errs), "max_abs_err_T": max(e[2] for e in errs),
             "runs_checked": len(errs),
             "wavelengths_nm": sorted({round(e[0] * 1e9) for e in errs}),
-            "vs": "FP64 oracle, same full-length runs (tests/golden/oracle_c2_*.json)",
+            "vs": ("FP64 oracle, same full-length runs (tests/golden/"
+                   + ("oracle_c2p_*.json)" if pol == "p" else "oracle_c2_*.json)")),
             "bound": 2e-3}
 
 

@@ -24,6 +24,44 @@ SRC = os.path.join(HERE, "tmz_loop.c")
 LIB = os.path.join(HERE, "_tmz_loop.so")
 
 
+def compile_loop(src: str, lib: str, force: bool = False) -> str:
+    """Compile one C time loop with gcc (OpenMP, no FP contraction so that
+    every product and sum rounds exactly as in numpy)."""
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
+        tmp = lib + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+               "-fno-fast-math", "-o", tmp, src]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"gcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, lib)
+    return lib
+
+
+def pml_pack(layers, ny, nx):
+    """The oracle's CPML layers ((rows, b, c, kappa, psi) per side) as the C
+    loops take them: a row -> CPML-row index map (-1 outside), the per-row
+    b, c, kappa and the psi rows stacked."""
+    idx = np.full(ny, -1, dtype=np.int32)
+    rows = [r for lay in layers for r in lay[0]]
+    idx[np.asarray(rows, dtype=np.int64)] = np.arange(len(rows), dtype=np.int32)
+    b = np.ascontiguousarray(np.concatenate([lay[1][:, 0] for lay in layers])) if rows else np.zeros(1)
+    c = np.ascontiguousarray(np.concatenate([lay[2][:, 0] for lay in layers])) if rows else np.zeros(1)
+    k = np.ascontiguousarray(np.concatenate([lay[3][:, 0] for lay in layers])) if rows else np.zeros(1)
+    psi = (np.ascontiguousarray(np.concatenate([lay[4] for lay in layers]))
+           if rows else np.zeros((1, nx)))
+    return idx, b, c, k, psi
+
+
+def pml_unpack(layers, psi):
+    """Copy the stacked psi rows back into the oracle's layers."""
+    o = 0
+    for lay in layers:
+        m = len(lay[0])
+        lay[4][...] = psi[o:o + m]
+        o += m
+
+
 class _Args(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("dx", ctypes.c_double),
                 ("ch_curl", ctypes.c_double), ("js", ctypes.c_int32), ("tfsf", ctypes.c_int32),
@@ -31,17 +69,8 @@ class _Args(ctypes.Structure):
 
 
 def build(force: bool = False) -> str:
-    """Compile the C loop with gcc (OpenMP, no FP contraction so that every
-    product and sum rounds exactly as in numpy)."""
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
-        tmp = LIB + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-               "-fno-fast-math", "-o", tmp, SRC]
-        r = subprocess.run(cmd, capture_output=True, text=True)
-        if r.returncode != 0:
-            raise RuntimeError(f"gcc failed for {SRC}:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+    """Compile the TMz C loop."""
+    return compile_loop(SRC, LIB, force)
 
 
 _lib = None
@@ -63,24 +92,6 @@ class TMzOracleC(TMzOracle):
     """TMzOracle whose run(steps) advances with the C loop."""
 
     threads = os.cpu_count() or 1
-
-    def _pml_pack(self, layers):
-        idx = np.full(self.ny, -1, dtype=np.int32)
-        rows = [r for lay in layers for r in lay[0]]
-        idx[np.asarray(rows, dtype=np.int64)] = np.arange(len(rows), dtype=np.int32)
-        b = np.ascontiguousarray(np.concatenate([lay[1][:, 0] for lay in layers])) if rows else np.zeros(1)
-        c = np.ascontiguousarray(np.concatenate([lay[2][:, 0] for lay in layers])) if rows else np.zeros(1)
-        k = np.ascontiguousarray(np.concatenate([lay[3][:, 0] for lay in layers])) if rows else np.zeros(1)
-        psi = (np.ascontiguousarray(np.concatenate([lay[4] for lay in layers]))
-               if rows else np.zeros((1, self.nx)))
-        return idx, b, c, k, psi
-
-    def _pml_unpack(self, layers, psi):
-        o = 0
-        for lay in layers:
-            m = len(lay[0])
-            lay[4][...] = psi[o:o + m]
-            o += m
 
     def run(self, steps, threads=None):
         steps = int(steps)
@@ -108,8 +119,8 @@ class TMzOracleC(TMzOracle):
         ce = np.ascontiguousarray(np.broadcast_to(self.ce, (self.ny, self.nx)), dtype=np.float64)
         cc = np.ascontiguousarray(np.broadcast_to(self.ce_curl, (self.ny, self.nx)),
                                   dtype=np.float64)
-        ei, eb, ec, ek, pe_ = self._pml_pack(self.pml_e)
-        hi, hb, hc, hk, ph_ = self._pml_pack(self.pml_h)
+        ei, eb, ec, ek, pe_ = pml_pack(self.pml_e, self.ny, self.nx)
+        hi, hb, hc, hk, ph_ = pml_pack(self.pml_h, self.ny, self.nx)
         dft = np.zeros((4, self.nx, 2))
         for q, key in enumerate(("e_r", "h_r", "e_t", "h_t")):
             dft[q, :, 0] = self.dft[key].real
@@ -124,8 +135,8 @@ class TMzOracleC(TMzOracle):
             _ptr(h_inc), _ptr(e_inc), _ptr(ph_e), _ptr(ph_h), _ptr(dft))
         if rc != 0:
             raise ValueError(f"tmz_loop_run rejected the grid (status {rc})")
-        self._pml_unpack(self.pml_e, pe_)
-        self._pml_unpack(self.pml_h, ph_)
+        pml_unpack(self.pml_e, pe_)
+        pml_unpack(self.pml_h, ph_)
         for q, key in enumerate(("e_r", "h_r", "e_t", "h_t")):
             v = np.empty(self.nx, dtype=np.complex128)
             v.real, v.imag = dft[q, :, 0], dft[q, :, 1]

@@ -7,6 +7,8 @@ and bench.py compare the CUDA library with these files.
   python tests/golden/make_oracle_goldens.py c2 550 [450 662 800 1450] [--threads N]
       config 2: the 2000 x 12500 dicot cross-section (seed 0), 30 000 steps
       at each wavelength (nm), S polarisation, as the throughput line runs it.
+  python tests/golden/make_oracle_goldens.py c2p 550 [1450 ...] [--threads N]
+      the same runs in P polarisation (the TEz oracle, its time loop in C).
   python tests/golden/make_oracle_goldens.py c3crop [--threads N]
       config 3 (healthy monocot, 550 nm, dx = 15 nm) cropped to its first
       8192 rows (the whole leaf and both monitors) and 2048 columns, with R, T
@@ -19,12 +21,14 @@ and bench.py compare the CUDA library with these files.
   python tests/golden/make_oracle_goldens.py e2 [--threads N]
       the validation cylinder array of Sec. 3 (100 x 897 cells, h = 0.01 m),
       60 000 steps, S and P polarisation, at L/lambda = 0.75, 0.82, 0.855
-      and 0.90 (the P runs use the numpy TEz oracle).
+      and 0.90.
 
 Each run writes oracle_<case>.json (scalars, with the command that made
 them) and oracle_<case>.npz (the four DFT lines, complex128, in the order
-Ez(r_row), Hx(r_row), Ez(t_row), Hx(t_row), and the fields Ez, Hx, Hy at
-4096 cells drawn with numpy's default_rng(2024), with their flat indices).
+Ez(r_row), Hx(r_row), Ez(t_row), Hx(t_row) for S and Hz(r_row), Ex(r_row),
+Hz(t_row), Ex(t_row) for P, and the fields Ez, Hx, Hy (S) or Hz, Ex, Ey (P)
+at 4096 cells drawn with numpy's default_rng(2024), with their flat
+indices, under the keys ez, hx, hy).
 """
 from __future__ import annotations
 
@@ -42,7 +46,8 @@ if ROOT not in sys.path:
 
 from fdtd_inputs import config_c2, config_c3, config_c5, config_e2, crop_layout  # noqa: E402
 from oracle import eps_sigma  # noqa: E402
-from oracle.fdtd_tez import TEzOracle, empty_twin_tez  # noqa: E402
+from oracle.fdtd_tez import empty_twin_tez  # noqa: E402
+from oracle.fdtd_tez_c import TEzOracleC  # noqa: E402
 from oracle.fdtd_tmz import empty_twin  # noqa: E402
 from oracle.fdtd_tmz_c import TMzOracleC  # noqa: E402
 
@@ -73,16 +78,20 @@ def _record(name, spec, leaf, twin, steps, wall, threads, cmd, extra=None):
         polarization="P (TEz)" if getattr(spec, "polarization", 0) else "S (TMz)",
         R=ratio(p_up), T=ratio(p_down),
         A=None if p_inc <= 0.0 else 1.0 - (p_up + p_down) / p_inc, p_up=p_up, p_down=p_down, p_inc=p_inc,
-        oracle="FP64 oracle (TMzOracle state, C time loop TMzOracleC)",
+        oracle=("FP64 oracle (TEzOracle state, C time loop TEzOracleC)"
+                if getattr(spec, "polarization", 0) else
+                "FP64 oracle (TMzOracle state, C time loop TMzOracleC)"),
         threads=int(threads), wall_s=round(wall, 1), command=cmd)
     if extra:
         rec.update(extra)
     idx = sample_index(spec.ny, spec.nx)
     d = leaf.dft
     fields = leaf.fields()                   # (Ez, Hx, Hy) or, for P, (Hz, Ex, Ey)
+    order = (("h_r", "e_r", "h_t", "e_t") if getattr(spec, "polarization", 0)
+             else ("e_r", "h_r", "e_t", "h_t"))
     np.savez_compressed(
         os.path.join(HERE, f"oracle_{name}.npz"),
-        dft=np.stack([d["e_r"], d["h_r"], d["e_t"], d["h_t"]]),
+        dft=np.stack([d[k] for k in order]),
         idx=idx, ez=fields[0].ravel()[idx], hx=fields[1].ravel()[idx],
         hy=fields[2].ravel()[idx], max_abs=np.array([np.abs(f).max() for f in fields]))
     with open(os.path.join(HERE, f"oracle_{name}.json"), "w") as f:
@@ -97,6 +106,16 @@ def run_c2(lam_nm, threads):
     twin = empty_twin(spec).run(spec.steps)
     _record(f"c2_{lam_nm:g}nm", spec, leaf, twin, spec.steps, time.time() - t, threads,
             f"python tests/golden/make_oracle_goldens.py c2 {lam_nm:g} --threads {threads}",
+            dict(seed=0))
+
+
+def run_c2p(lam_nm, threads):
+    spec = config_c2(lam_nm * 1e-9).with_(polarization=1)
+    t = time.time()
+    leaf = TEzOracleC(spec).run(spec.steps, threads)
+    twin = empty_twin_tez(spec).run(spec.steps)
+    _record(f"c2p_{lam_nm:g}nm", spec, leaf, twin, spec.steps, time.time() - t, threads,
+            f"python tests/golden/make_oracle_goldens.py c2p {lam_nm:g} --threads {threads}",
             dict(seed=0))
 
 
@@ -124,13 +143,13 @@ def run_e2(threads):
             spec = config_e2(x, steps=60000).with_(polarization=pol)
             t = time.time()
             if pol:
-                leaf = TEzOracle(spec).run(spec.steps)
+                leaf = TEzOracleC(spec).run(spec.steps, threads)
                 twin = empty_twin_tez(spec).run(spec.steps)
             else:
                 leaf = TMzOracleC(spec).run(spec.steps, threads)
                 twin = empty_twin(spec).run(spec.steps)
             _record(f"e2_{'SP'[pol]}_{x:g}", spec, leaf, twin, spec.steps, time.time() - t,
-                    threads if not pol else 1,
+                    threads,
                     f"python tests/golden/make_oracle_goldens.py e2 --threads {threads}",
                     dict(l_over_lambda=x))
 
@@ -198,6 +217,9 @@ def main(argv):
     if case == "c2":
         for lam in argv[1:] or ["550"]:
             run_c2(float(lam), threads)
+    elif case == "c2p":
+        for lam in argv[1:] or ["550"]:
+            run_c2p(float(lam), threads)
     elif case == "c3crop":
         run_c3crop(threads)
     elif case == "e2":

@@ -71,6 +71,10 @@ def test_golden_rt_check_compares_matching_runs(monkeypatch, tmp_path):
     assert bench.golden_rt_check(res, 1000, "s") is None
     # the stored runs are S-polarised: a P line has nothing to compare with
     assert bench.golden_rt_check(res, 30000, "p") is None
+    (g / "oracle_c2p_550nm.json").write_text(
+        json.dumps({"steps": 30000, "R": 0.2, "T": 0.4, "polarization": "P (TEz)"}))
+    d = bench.golden_rt_check(res, 30000, "p")
+    assert d["runs_checked"] == 1 and abs(d["max_abs_err_R"] - 0.0996) < 1e-12
 
 
 def test_issue_fraction_of_the_roofline_record(monkeypatch):

@@ -5,7 +5,7 @@ only the oracle (its C time loop, bit-identical to the numpy loop):
 
 * config 2: the 2000 x 12500 dicot cross-section, 30 000 steps, at each
   wavelength the throughput line cycles through (the workload the metric is
-  quoted on);
+  quoted on), and in P polarisation (TEz) where a P run is stored;
 * config 3: the healthy monocot at 550 nm cropped to 8192 x 2048 cells (the
   whole leaf and both monitors), after 4000 and after 60 000 steps.
 
@@ -50,6 +50,7 @@ def _golden(pattern):
 
 
 C2 = _golden("oracle_c2_*nm.json")
+C2P = _golden("oracle_c2p_*nm.json")
 C3 = _golden("oracle_c3crop_*.json")
 
 
@@ -65,7 +66,7 @@ def c2_labels():
     return config_c2().labels
 
 
-def _compare(sim, rec, ref, name):
+def _compare(sim, rec, ref, name, pol=0):
     R, T = sim.flux() if rec["R"] is not None else (None, None)
     raw = sim.flux_raw()
     d = sim.dft()
@@ -79,9 +80,10 @@ def _compare(sim, rec, ref, name):
             assert np.all(d[q] == 0.0), name
             continue
         line_err.append(float(np.abs(d[q] - ref["dft"][q]).max() / scale))
-    # E and eta0 H have the same scale
-    g = np.concatenate([ez.ravel()[idx], hx.ravel()[idx] * ETA0, hy.ravel()[idx] * ETA0])
-    r = np.concatenate([ref["ez"], ref["hx"] * ETA0, ref["hy"] * ETA0])
+    # E and eta0 H have the same scale; the P fields are (Hz, Ex, Ey)
+    sc = (ETA0, 1.0, 1.0) if pol else (1.0, ETA0, ETA0)
+    g = np.concatenate([ez.ravel()[idx] * sc[0], hx.ravel()[idx] * sc[1], hy.ravel()[idx] * sc[2]])
+    r = np.concatenate([ref["ez"] * sc[0], ref["hx"] * sc[1], ref["hy"] * sc[2]])
     f_err = float(np.linalg.norm(g - r) / np.linalg.norm(r))
     p_err = [abs(a - b) / abs(b) for a, b in zip(raw, (rec["p_up"], rec["p_down"], rec["p_inc"]))
              if b != 0.0]
@@ -108,6 +110,19 @@ def test_config2_full_run_matches_oracle(fd, c2_labels, case):
         sim.run(spec.steps)
         assert sim.stats()["kernel"] == 2
         _compare(sim, rec, ref, rec["case"])
+
+
+@pytest.mark.skipif(not C2P, reason="no P-polarised config-2 oracle goldens written")
+@pytest.mark.parametrize("case", range(len(C2P)), ids=[c[0]["case"] for c in C2P])
+def test_config2_p_full_run_matches_oracle(fd, c2_labels, case):
+    from fdtd_inputs import config_c2
+    rec, ref = C2P[case]
+    spec = config_c2(rec["lambda0"], labels=c2_labels, steps=rec["steps"]).with_(polarization=1)
+    assert (spec.nx, spec.ny) == (rec["nx"], rec["ny"]) and rec["polarization"].startswith("P")
+    with fd.Simulation(spec) as sim:               # the default path of the P bench line
+        sim.run(spec.steps)
+        assert sim.stats()["kernel"] == 2
+        _compare(sim, rec, ref, rec["case"], pol=1)
 
 
 @pytest.mark.skipif(not C3, reason="no config-3 crop oracle goldens written")
