@@ -284,7 +284,8 @@ void fdtd_destroy(fdtd_handle* h);
  * (last first) the steps are recomputed from their checkpoint, storing for
  * each step the two forward factors of the gradient sums (Ez before the
  * update and the factor of cb in it) on a device tape (about 8*every bytes
- * per cell plus two states, freed on return), and the transpose of every
+ * per cell plus two states; the handle keeps it for the next fdtd_backward
+ * of the same size and fdtd_destroy frees it), and the transpose of every
  * update is applied in reverse order; per-segment FP32 sums are accumulated
  * in FP64. The handle keeps its final forward
  * state. FDTD_ESTATE if no checkpointed run precedes or no incident power

@@ -970,18 +970,12 @@ int fdtd_forward_checkpointed(fdtd_handle* h, int64_t steps, int32_t every) {
 int fdtd_backward(fdtd_handle* h, double wR, double wT, double* g_eps, double* g_sigma,
                   double* g_label, double out[3]) {
     if (!h) return FDTD_EINVAL;
-    std::vector<float*> tape;
     std::vector<AdjPlan> adj_plans;
-    float* st[2] = {nullptr, nullptr};
     float* buf = nullptr;
     double* dbl = nullptr;
     double2* dummy = nullptr;
-    float** d_tape_ptrs = nullptr;
     auto cleanup = [&]() {
         for (auto& pl : adj_plans) if (pl.d_seg) cudaFree(pl.d_seg);
-        if (d_tape_ptrs) cudaFree(d_tape_ptrs);
-        for (auto& t : tape) cudaFree(t);
-        for (float* q : st) if (q) cudaFree(q);
         if (buf) cudaFree(buf);
         if (dbl) cudaFree(dbl);
         if (dummy) cudaFree(dummy);
@@ -1010,19 +1004,31 @@ int fdtd_backward(fdtd_handle* h, double wR, double wT, double* g_eps, double* g
         const int every = h->adj_every;
         const int64_t steps = h->adj_steps;
         // the tape: per step of a segment, Ez^{n-1/2} and the factor of cb
-        // (f floats each); two state buffers carry the recompute
+        // (f floats each); two state buffers carry the recompute; a device
+        // array holds the tape steps' base pointers for the multi-step
+        // recompute (labelled grids with nx % 4 == 0). The handle keeps them
+        // for the next fdtd_backward of the same size.
         const size_t sf = state_floats(h);
-        tape.assign((size_t)std::min<int64_t>(every, steps), nullptr);
-        for (auto& t : tape) ACK(cudaMalloc(&t, 2 * f * sizeof(float)));
-        for (float*& q : st) ACK(cudaMalloc(&q, sf * sizeof(float)));
-        // multi-step recompute (labelled grids with nx % 4 == 0): a device
-        // array of the tape steps' base pointers
-        const bool multi = !h->maps && nx % 4 == 0;
-        if (multi) {
-            ACK(cudaMalloc(&d_tape_ptrs, tape.size() * sizeof(float*)));
-            ACK(cudaMemcpy(d_tape_ptrs, tape.data(), tape.size() * sizeof(float*),
+        const size_t n_tape = (size_t)std::min<int64_t>(every, steps);
+        if (h->adj_tape.size() != n_tape || h->adj_tape_floats != 2 * f) {
+            ACK(cudaStreamSynchronize(h->stream));
+            for (auto& t : h->adj_tape) cudaFree(t);
+            for (float*& q : h->adj_state) { if (q) cudaFree(q); q = nullptr; }
+            if (h->d_adj_tape_ptrs) cudaFree(h->d_adj_tape_ptrs);
+            h->d_adj_tape_ptrs = nullptr;
+            h->adj_tape.assign(n_tape, nullptr);
+            h->adj_tape_floats = 0;
+            for (auto& t : h->adj_tape) ACK(cudaMalloc(&t, 2 * f * sizeof(float)));
+            for (float*& q : h->adj_state) ACK(cudaMalloc(&q, sf * sizeof(float)));
+            ACK(cudaMalloc(&h->d_adj_tape_ptrs, n_tape * sizeof(float*)));
+            ACK(cudaMemcpy(h->d_adj_tape_ptrs, h->adj_tape.data(), n_tape * sizeof(float*),
                            cudaMemcpyHostToDevice));
+            h->adj_tape_floats = 2 * f;
         }
+        const std::vector<float*>& tape = h->adj_tape;
+        float* const* st = h->adj_state;
+        float* const* d_tape_ptrs = h->d_adj_tape_ptrs;
+        const bool multi = !h->maps && nx % 4 == 0;
         // lE[2] lX lY gA gB (f each) + mE[2] mH[2] (pr each) + the second lX, lY
         // buffers of the blocked reverse kernel (f each)
         ACK(cudaMalloc(&buf, (8 * f + 4 * pr) * sizeof(float)));

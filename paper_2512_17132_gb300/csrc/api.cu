@@ -541,6 +541,10 @@ void free_all(fdtd_handle* h) {
     dfree(h->cellcoef); dfree(h->cell_eps); dfree(h->cell_sig);
     for (auto& c : h->ck) dfree(c);
     h->ck.clear();
+    for (auto& t : h->adj_tape) dfree(t);
+    h->adj_tape.clear();
+    for (float*& q : h->adj_state) { dfree(q); q = nullptr; }
+    if (h->d_adj_tape_ptrs) { cudaFree(h->d_adj_tape_ptrs); h->d_adj_tape_ptrs = nullptr; }
     dfree(h->tw_ez); dfree(h->tw_hx); dfree(h->tw_psiE); dfree(h->tw_psiH); dfree(h->tw_dft);
     dfree(h->d_flux); dfree(h->d_flag); dfree(h->d_dbg);
     h->guarded.clear();

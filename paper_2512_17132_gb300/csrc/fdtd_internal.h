@@ -201,6 +201,13 @@ struct fdtd_handle {
     // adjoint: checkpoints of the last fdtd_forward_checkpointed run
     std::vector<float*> ck;             // state at steps 0, every, 2 every, ...
     size_t ck_floats = 0;
+    // fdtd_backward's tape (per step of a segment, the gradient factors), the
+    // recompute's two state buffers and the device array of tape pointers:
+    // kept for the next fdtd_backward of the same size, freed by fdtd_destroy
+    std::vector<float*> adj_tape;
+    size_t adj_tape_floats = 0;
+    float* adj_state[2] = {nullptr, nullptr};
+    float** d_adj_tape_ptrs = nullptr;
     int64_t adj_steps = 0;
     int adj_every = 0;
     bool adj_valid = false;
