@@ -492,7 +492,9 @@ class Simulation:
         return self
 
     def gradient(self, steps, wR=1.0, wT=0.0, every=500):
-        """Forward with checkpoints, then the discrete adjoint of wR R + wT T."""
+        """Forward with checkpoints, then the discrete adjoint of wR R + wT T.
+        The handle keeps the checkpoints and the backward pass's tape (about
+        8 * every bytes per cell) for the next gradient; close() frees them."""
         fdtd_forward_checkpointed(self.h, steps, every)
         n_lab = 0 if getattr(self, "_maps", False) else len(self.spec.materials)
         return fdtd_backward(self.h, wR, wT, self.spec.ny, self.spec.nx, n_lab)
