@@ -13,6 +13,8 @@ and bench.py compare the CUDA library with these files.
       config 3 (healthy monocot, 550 nm, dx = 15 nm) cropped to its first
       8192 rows (the whole leaf and both monitors) and 2048 columns, with R, T
       and the DFT lines after 4000 and after 60 000 steps.
+  python tests/golden/make_oracle_goldens.py c3cropp [--threads N]
+      the same crop in P polarisation (the TEz oracle, its time loop in C).
   python tests/golden/make_oracle_goldens.py c5fd [--threads N]
       config 5 (the config-1 stack at 1000 x 6000, 550 nm) over 6000 steps:
       R and its central differences (h = 1e-4) with respect to eps_r at 32
@@ -119,18 +121,19 @@ def run_c2p(lam_nm, threads):
             dict(seed=0))
 
 
-def run_c3crop(threads):
-    spec = c3_crop_spec()
+def run_c3crop(threads, pol=0):
+    spec = c3_crop_spec().with_(polarization=pol)
+    name = "c3cropp" if pol else "c3crop"
     t = time.time()
-    leaf = TMzOracleC(spec)
-    twin = empty_twin(spec)
+    leaf = TEzOracleC(spec) if pol else TMzOracleC(spec)
+    twin = empty_twin_tez(spec) if pol else empty_twin(spec)
     done = 0
     for steps in (4000, 60000):
         leaf.run(steps - done, threads)
         twin.run(steps - done)
         done = steps
-        _record(f"c3crop_{steps}", spec, leaf, twin, steps, time.time() - t, threads,
-                f"python tests/golden/make_oracle_goldens.py c3crop --threads {threads}",
+        _record(f"{name}_{steps}", spec, leaf, twin, steps, time.time() - t, threads,
+                f"python tests/golden/make_oracle_goldens.py {name} --threads {threads}",
                 dict(seed=0, crop="config 3 healthy, rows 0-8191, columns 0-2047"))
 
 
@@ -222,6 +225,8 @@ def main(argv):
             run_c2p(float(lam), threads)
     elif case == "c3crop":
         run_c3crop(threads)
+    elif case == "c3cropp":
+        run_c3crop(threads, pol=1)
     elif case == "e2":
         run_e2(threads)
     elif case == "c5fd":

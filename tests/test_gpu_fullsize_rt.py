@@ -7,7 +7,8 @@ only the oracle (its C time loop, bit-identical to the numpy loop):
   wavelength the throughput line cycles through (the workload the metric is
   quoted on), and in P polarisation (TEz) where a P run is stored;
 * config 3: the healthy monocot at 550 nm cropped to 8192 x 2048 cells (the
-  whole leaf and both monitors), after 4000 and after 60 000 steps.
+  whole leaf and both monitors), after 4000 and after 60 000 steps, in both
+  polarisations.
 
 Bounds. R and T: 2e-3 absolute (the parity requirement of the scope); the
 first config-2 comparison measured 3e-7 and 9e-8 (550 nm). The
@@ -52,6 +53,7 @@ def _golden(pattern):
 C2 = _golden("oracle_c2_*nm.json")
 C2P = _golden("oracle_c2p_*nm.json")
 C3 = _golden("oracle_c3crop_*.json")
+C3P = _golden("oracle_c3cropp_*.json")
 
 
 @pytest.fixture(scope="module")
@@ -137,3 +139,17 @@ def test_config3_crop_matches_oracle(fd):
             sim.run(rec["steps"] - done)
             done = rec["steps"]
             _compare(sim, rec, ref, rec["case"])
+
+
+@pytest.mark.skipif(not C3P, reason="no P-polarised config-3 crop oracle goldens written")
+def test_config3_crop_p_matches_oracle(fd):
+    from fdtd_inputs import config_c3, crop_layout
+    spec = crop_layout(config_c3(550e-9), 8192, 2048).with_(polarization=1)
+    runs = sorted(C3P, key=lambda c: c[0]["steps"])
+    with fd.Simulation(spec) as sim:
+        done = 0
+        for rec, ref in runs:
+            assert (spec.nx, spec.ny) == (rec["nx"], rec["ny"]) and rec["polarization"].startswith("P")
+            sim.run(rec["steps"] - done)
+            done = rec["steps"]
+            _compare(sim, rec, ref, rec["case"], pol=1)
